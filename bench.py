@@ -1,0 +1,488 @@
+"""Benchmark of the regularized-Stokeslet pair sum on GB300 (one JSON line on stdout).
+
+Workload (one "step"): one mrs_velocity call, float32 with compensated accumulation, on the
+single-system configuration -- 32 filaments x 1024 nodes = 32768 points in a 10^3 box with
+random orientations, eps = 1.5 ds, mu = 1, Gaussian forces and torques (seeded, synthetic).
+Metric: pair interactions per second (N^2 ordered pairs, self included), with the fraction of
+the FP32 (non-tensor) peak and the relative L2 error of a sampled set of targets against the
+FP64 oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+
+--impl reference times the FP64 CPU oracle (the only reference there is) on the same workload,
+each step a bounded sample of targets.  For N > 1 (torchrun), every rank runs its own replica
+(replicas only: the path needs no exchange between GPUs), and value = all ranks' pairs / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_PAIR = 92          # canonical algorithmic flop count of one ordered pair
+METRIC = "MRS pair-interactions/s"
+UNIT = "pairs/s"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(n_sms, peaks):
+    """2 flops (FMA) x 128 FP32 lanes per SM x SMs x the maximum SM clock."""
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return 2.0 * 128 * n_sms * mhz * 1e6 / 1e12, mhz
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.gpu_id = gpu_id
+        self.path = os.path.join("/tmp", "mrs_clocks_%d_%d.csv" % (os.getpid(), int(time.time())))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, dev):
+    import torch
+    torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier(device_ids=[dev.index])
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(pg, value, dev):
+    import torch
+    if pg is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, value, dev):
+    import torch
+    if pg is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_rate(p, seconds_target, seed=0):
+    """Pairs/s of the FP64 oracle on a sample of targets of problem p (all sources)."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    N = p.n_points
+    # calibrate on 64 targets, then size the sample to ~seconds_target
+    idx = rng.choice(N, 64, replace=False)
+    t0 = time.perf_counter()
+    oracle.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu, xt=p.X[idx])
+    dt = max(time.perf_counter() - t0, 1e-6)
+    rate = 64 * N / dt
+    nt = int(min(N, max(64, seconds_target * rate / N)))
+    return nt, rate
+
+
+def run_reference(args, world, rank):
+    """The oracle arm: FP64 CPU oracle on the same workload, bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2604_12083_gb300 import workloads as W
+    p = W.single_system()
+    budget = 150.0 / max(1, args.steps + args.warmup)     # whole run within a few minutes
+    nt, _ = oracle_rate(p, budget)
+    rng = np.random.default_rng(5)
+    times = []
+    for it in range(args.warmup + args.steps):
+        idx = rng.choice(p.n_points, nt, replace=False)
+        t0 = time.perf_counter()
+        oracle.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu, xt=p.X[idx])
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    pairs = nt * p.n_points
+    value = pairs * len(times) / sum(times)
+    cores = oracle.num_threads()
+    sample = "%d sampled targets x %d sources per step (FP64, OpenMP over targets)" % (nt, p.n_points)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": p.name, "n_points": p.n_points, "eps": float(p.eps[0]), "mu": p.mu,
+                   "parallelism": "none (host cores)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _time_events(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extra_batch(ctx, dev):
+    """512 systems (256..16384 points): one persistent launch (CUDA graph) vs one launch per
+    system, float32 accumulation; rel L2 of 4 sampled targets per system."""
+    import torch
+    import oracle
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.batch_systems()
+    X, f, n = (torch.from_numpy(a).to(dev) for a in (p.X, p.f, p.n))
+    u = torch.empty_like(X)
+    w = torch.empty_like(X)
+    stream = torch.cuda.current_stream(dev)
+    plan = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32)
+    plan.execute(X, f, n, u, w)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            plan.execute(X, f, n, u, w, stream=side)
+    stream.wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    ms_graph = _time_events(g.replay, 5, stream)
+    rng = np.random.default_rng(12)
+    en = ed = wn = wd = 0.0
+    ug, wg = u.cpu().numpy().astype(np.float64), w.cpu().numpy().astype(np.float64)
+    for s in range(0, len(p.offsets) - 1):
+        a, b = int(p.offsets[s]), int(p.offsets[s + 1])
+        idx = rng.choice(b - a, 4, replace=False)
+        ur, wr = oracle.mrs_velocity(p.X[a:b], p.f[a:b], p.n[a:b], p.eps[s], p.mu, xt=p.X[a:b][idx])
+        en += np.sum((ug[a:b][idx] - ur) ** 2); ed += np.sum(ur ** 2)
+        wn += np.sum((wg[a:b][idx] - wr) ** 2); wd += np.sum(wr ** 2)
+    rel_batch = {"u": float(np.sqrt(en / ed)), "w": float(np.sqrt(wn / wd))}
+    plans = []
+    for s in range(len(p.offsets) - 1):
+        a, b = int(p.offsets[s]), int(p.offsets[s + 1])
+        plans.append((a, b, mrs.Plan(ctx, [0, b - a], p.mu, float(p.eps[s]), precision=mrs.MRS_F32)))
+    views = [(X[a:b], f[a:b], n[a:b], u[a:b], w[a:b], pl) for a, b, pl in plans]
+
+    def loop():
+        for xx, ff, nn, uu, ww, pl in views:
+            pl.execute(xx, ff, nn, uu, ww)
+
+    loop()
+    torch.cuda.synchronize()
+    ms_loop = _time_events(loop, 3, stream)
+    for _, _, pl in plans:
+        pl.close()
+    info = plan.info()
+    plan.close()
+    return {"workload": p.name + " (N_s log-uniform in [256,16384], filaments of 256 nodes)",
+            "pairs": p.pairs, "persistent_graph_ms": ms_graph,
+            "persistent_pairs_per_s": p.pairs / (ms_graph * 1e-3),
+            "one_launch_per_system_ms": ms_loop,
+            "one_launch_per_system_pairs_per_s": p.pairs / (ms_loop * 1e-3),
+            "speedup": ms_loop / ms_graph, "rel_err_sampled": rel_batch, "plan": info}
+
+
+def extra_rod_step(ctx, dev):
+    """One rod of 128 nodes: 200 Euler and 200 RK2 steps at dt = 1e-6 (graph replays)."""
+    import torch
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(1, 1, 128)
+    c = W.ROD_PLAIN
+    prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"], 1.0, rs.eps)
+    out = {"workload": "one rod, 128 nodes, 200 steps, dt=1e-6"}
+    stream = torch.cuda.current_stream(dev)
+    for name, sch in (("euler", mrs.MRS_EULER), ("rk2", mrs.MRS_RK2)):
+        Xd, Dd = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
+        mrs.rod_step(ctx, rs.rod_off, prm, Xd, Dd, 0.0, c["dt"], 200, sch)
+        torch.cuda.synchronize()
+        ms = _time_events(lambda: mrs.rod_step(ctx, rs.rod_off, prm, Xd, Dd, 0.0, c["dt"], 200, sch),
+                          3, stream)
+        out[name + "_us_per_step"] = 1e3 * ms / 200
+    return out
+
+
+def extra_parareal(ctx, dev):
+    """8 filaments x 512 nodes, 64 slices, fine RK2 dt = 1e-6, coarse Euler 16 dt, over a
+    shortened horizon (16 fine steps per slice); compared with serial fine RK2 on the GPU."""
+    import torch
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(4, 8, 512)
+    c = W.ROD_PARAREAL
+    prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"], 1.0, rs.eps)
+    Ns, nf, r, dt = 64, 16, 16, c["dt"]
+    T1 = Ns * nf * dt
+    Xs, Ds = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
+    mrs.rod_step(ctx, rs.rod_off, prm, Xs, Ds, 0.0, dt, 16, mrs.MRS_RK2)   # warm-up / capture
+    Xs, Ds = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mrs.rod_step(ctx, rs.rod_off, prm, Xs, Ds, 0.0, dt, Ns * nf, mrs.MRS_RK2)
+    torch.cuda.synchronize()
+    t_serial = time.perf_counter() - t0
+    Xp, Dp = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
+    st = mrs.parareal_run(ctx, rs.rod_off, prm, Xp, Dp, 0.0, T1, Ns, dt, r, 8, 1e-11,
+                          raise_on_noconv=False)
+    Xp, Dp = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
+    st = mrs.parareal_run(ctx, rs.rod_off, prm, Xp, Dp, 0.0, T1, Ns, dt, r, 8, 1e-11,
+                          raise_on_noconv=False)
+    x0 = rs.X
+    disp_s = Xs.cpu().numpy() - x0
+    disp_p = Xp.cpu().numpy() - x0
+    return {"workload": "8 filaments x 512 nodes, 64 slices x 16 fine RK2 steps (dt=1e-6), coarse 16 dt",
+            "iterations": st.iterations, "increments": [st.incr[i] for i in range(st.iterations)],
+            "parareal_s": st.seconds, "serial_fine_s": t_serial,
+            "fine_steps_executed": st.fine_steps, "serial_fine_steps": Ns * nf,
+            "rel_diff_vs_serial_displacement": float(np.linalg.norm(disp_p - disp_s) / np.linalg.norm(disp_s))}
+
+
+def run_extras(ctx, dev):
+    out = {}
+    for name, fn in (("batch", extra_batch), ("rod_step", extra_rod_step),
+                     ("parareal", extra_parareal)):
+        try:
+            out[name] = fn(ctx, dev)
+        except Exception as e:       # reported, never silently replaced by another path
+            out[name] = {"error": repr(e)}
+    return out
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    from paper_2604_12083_gb300 import build as B, mrs, workloads as W
+    if rank == 0 or not os.path.exists(mrs.LIB_PATH):
+        B.build()
+    if pg is not None:
+        pg.barrier()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = mrs.Context(local)
+    p = W.single_system(seed=2 + rank)      # each rank: its own replica of the workload
+    stream = torch.cuda.current_stream(dev)
+    X, f, n = (torch.from_numpy(a).to(dev) for a in (p.X, p.f, p.n))
+    u = torch.empty_like(X)
+    w = torch.empty_like(X)
+    eps = float(p.eps[0])
+
+    def step():
+        mrs.mrs_velocity(ctx, p.offsets, X, f, n, u, w, p.mu, eps, precision=mrs.MRS_F32_COMP)
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MiB > L2
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: K steps, L2 flushed before each, events around each launch ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(pg, dev)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier(pg, dev)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = sum(launch_ms)
+    t_max = max_over_ranks(pg, t_ms, dev)
+    pairs_all = sum_over_ranks(pg, float(p.pairs) * args.steps, dev)
+    value = pairs_all / (t_max * 1e-3)
+    ms_per_step = t_max / args.steps
+
+    # ---- parity on sampled targets (oracle, rank 0 only; outside the timed region) ----
+    rel = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        idx = np.random.default_rng(9).choice(p.n_points, 256, replace=False)
+        ur, wr = oracle.mrs_velocity(p.X, p.f, p.n, eps, p.mu, xt=p.X[idx])
+        ug = u.cpu().numpy().astype(np.float64)[idx]
+        wg = w.cpu().numpy().astype(np.float64)[idx]
+        rel = {"u": float(np.linalg.norm(ug - ur) / np.linalg.norm(ur)),
+               "w": float(np.linalg.norm(wg - wr) / np.linalg.norm(wr)),
+               "targets_sampled": 256}
+
+    # ---- end to end through the public API with host buffers ----
+    hX, hf, hn = (torch.from_numpy(a).pin_memory() for a in (p.X, p.f, p.n))
+    hu = torch.empty(u.shape, dtype=u.dtype).pin_memory()
+    hw = torch.empty(w.shape, dtype=w.dtype).pin_memory()
+    dX, df, dn = torch.empty_like(X), torch.empty_like(f), torch.empty_like(n)
+    du, dw = torch.empty_like(u), torch.empty_like(w)
+
+    def e2e_step():
+        dX.copy_(hX, non_blocking=True)
+        df.copy_(hf, non_blocking=True)
+        dn.copy_(hn, non_blocking=True)
+        mrs.mrs_velocity(ctx, p.offsets, dX, df, dn, du, dw, p.mu, eps, precision=mrs.MRS_F32_COMP)
+        hu.copy_(du, non_blocking=True)
+        hw.copy_(dw, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(10, min(args.steps, 200))
+    barrier(pg, dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    barrier(pg, dev)
+    e_ms = max_over_ranks(pg, e0.elapsed_time(e1), dev)
+    e2e_pairs = sum_over_ranks(pg, float(p.pairs) * e2e_steps, dev)
+    h2d = int(sum(t.numel() * t.element_size() for t in (hX, hf, hn)))
+    d2h = int(sum(t.numel() * t.element_size() for t in (hu, hw)))
+
+    peaks = load_peaks()
+    peak, mhz = fp32_peak_tflops(ctx.num_sms, peaks)
+    achieved = FLOPS_PER_PAIR * p.pairs / (np.mean(launch_ms) * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": p.name + " (32768 points, eps=1.5ds, mu=1, Gaussian f/n, "
+                   "FP32 compensated accumulation)", "n_points": p.n_points,
+                   "pairs_per_step": p.pairs, "global_batch": world, "parallelism":
+                   "replicas (one independent system per GPU)",
+                   "l2": "flushed before every timed step (512 MiB write)"},
+        "rel_err": rel,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "2 x 128 FP32 lanes x %d SMs x %.0f MHz (max SM clock)" %
+                                   (ctx.num_sms, mhz),
+                     "flops_per_pair": FLOPS_PER_PAIR, "kernel": "mrs_f32_persistent"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_pairs / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and args.cpu_baseline:
+        import oracle
+        nt, _ = oracle_rate(p, 10.0)
+        idx = np.random.default_rng(11).choice(p.n_points, nt, replace=False)
+        t0 = time.perf_counter()
+        oracle.mrs_velocity(p.X, p.f, p.n, eps, p.mu, xt=p.X[idx])
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nt * p.n_points / dt, "unit": UNIT,
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": "%d sampled targets x %d sources (FP64)" % (nt, p.n_points)}
+    if rank == 0 and args.extras:
+        line["extras"] = run_extras(ctx, dev)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local, pg = (1, 0, 0, None)
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, world, rank)
+        return
+    world, rank, local, pg = dist_setup()
+    run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * mrs_gb300.h -- C ABI of the GB300 (sm_103a) regularized-Stokeslet filament library.
+ *
+ * Method: "Accelerating Microswimmer Simulations via a Heterogeneous Pipelined
+ * Parallel-in-Time Framework" -- Kirchhoff-rod filaments coupled through the Method of
+ * Regularized Stokeslets (MRS), advanced in time by explicit Euler / RK2 and by Parareal.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an int status: MRS_OK (0) or one of the MRS_E* codes below.  On an
+ *    error, mrs_last_error() returns a message for the calling thread.  No call aborts the
+ *    process; invalid arguments are rejected before anything is launched.
+ *  - Pointers named "device" must point to device memory of the context's GPU; "host"
+ *    pointers to host memory.  The CALLER owns every buffer passed in: the library never frees
+ *    or retains caller memory beyond the call (plans keep only their own tables).
+ *  - Point arrays are AoS, row-major: p[k*3 + c] is component c of point k.  Frames are
+ *    D[k*9 + i*3 + c]: component c of director D^{i+1} of node k (rows are directors).
+ *  - Independent systems (or rods) are concatenated along the point axis and delimited by
+ *    CSR offsets: offsets[0] = 0 <= offsets[1] <= ... <= offsets[n] = total points.
+ *  - Work is enqueued on the caller's CUDA stream (`stream`, a cudaStream_t passed as void*;
+ *    NULL = the legacy default stream) and the call returns without synchronizing, except
+ *    where an entry point says otherwise.
+ *  - The library allocates device memory only in the plan
+ *    constructors, the first call of mrs_velocity for a given problem shape (which builds and
+ *    caches a plan) and the rod/Parareal/serving set-up calls -- never on a repeated call of
+ *    the same shape.  Warm a shape up before capturing its calls in a CUDA graph.
+ */
+#ifndef MRS_GB300_H
+#define MRS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MRS_API __attribute__((visibility("default")))
+#else
+#define MRS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define MRS_OK        0   /* success */
+#define MRS_EINVAL    1   /* invalid argument (sizes, offsets, eps <= 0, mu <= 0, NULL, ...) */
+#define MRS_ENOMEM    2   /* device or host allocation failed */
+#define MRS_ECUDA     3   /* a CUDA runtime call or kernel launch failed */
+#define MRS_ETIMEOUT  4   /* a bounded device-side wait ran out (the kernel returned early) */
+#define MRS_ENOCONV   5   /* Parareal did not reach the tolerance, or its increment diverged */
+#define MRS_EBUSY     6   /* serving: no free slot / budget for the job right now */
+#define MRS_PENDING   7   /* serving: the job has not finished yet */
+
+/* ---- arithmetic of the pair sum ---------------------------------------------------------- */
+#define MRS_F64       0   /* float64 inputs/outputs, float64 arithmetic */
+#define MRS_F32       1   /* float32 inputs/outputs, float32 arithmetic and accumulation */
+#define MRS_F32_COMP  2   /* float32 inputs/outputs, float32 arithmetic, compensated
+                             (Kahan-folded per-chunk partials) per-target accumulation */
+
+/* ---- time-stepping schemes (Section III-B) ----------------------------------------------- */
+#define MRS_EULER     0   /* explicit Euler, Eqs. newx / newD (the coarse propagator G) */
+#define MRS_RK2       1   /* second-order Runge-Kutta, explicit midpoint (the fine propagator F) */
+
+typedef struct mrs_ctx mrs_ctx;
+typedef struct mrs_plan mrs_plan;
+
+/* Message of the last failed call made by this thread ("" if none).  Valid until the next call. */
+MRS_API const char* mrs_last_error(void);
+
+/* Library version string. */
+MRS_API const char* mrs_version(void);
+
+/* Create a context on CUDA device `device` (the calling thread's current device is set to it).
+ * Queries the device (must be compute capability 10.3) and records SM count and limits.
+ * Errors: MRS_EINVAL (no such device or wrong architecture), MRS_ECUDA. */
+MRS_API int mrs_ctx_create(mrs_ctx** ctx, int device);
+
+/* Destroy a context and every plan it still owns.  Synchronizes the device first. */
+MRS_API int mrs_ctx_destroy(mrs_ctx* ctx);
+
+/* Number of SMs of the context's device (host-side query; no GPU work). */
+MRS_API int mrs_ctx_num_sms(const mrs_ctx* ctx);
+
+/* ==========================================================================================
+ * MRS pair sum -- Section II-C, Eqs. (velocity_field), (angular_velocity_field),
+ * (superposition); Section III-C-2.
+ *
+ * For every target i of system s and every source j of the same system (the self pair
+ * included; every kernel is finite at r = 0):
+ *     u_i     = (1/mu) sum_j [ f_j H1 + (f_j.r) r H2 + (n_j x r) H3 ]
+ *     omega_i = (1/mu) sum_j [ (f_j x r) H3 + n_j H4 + (n_j.r) r H5 ],    r = x_i - X_j,
+ * with the regularized kernels of the blob phi_eps(r) = 15 eps^4 / (8 pi (r^2+eps^2)^{7/2}):
+ *     H1 = (r^2+2e^2)/(8 pi d^{3/2}),  H2 = 1/(8 pi d^{3/2}),  H3 = (2r^2+5e^2)/(16 pi d^{5/2}),
+ *     H4 = (10e^4-7e^2r^2-2r^4)/(32 pi d^{7/2}),  H5 = (6r^2+21e^2)/(32 pi d^{7/2}),
+ * d = r^2 + eps^2 (H1, H2 as in the paper's cited source; H3..H5 from omega = curl(u)/2).
+ * ========================================================================================== */
+
+/* One call of the pair sum over n_sys independent systems.
+ *   offsets      host int64[n_sys+1], CSR point offsets (system s = points offsets[s]..offsets[s+1])
+ *   X, f, n      device [N][3] source positions, forces, torques (N = offsets[n_sys]);
+ *                float32 for MRS_F32 / MRS_F32_COMP, float64 for MRS_F64
+ *   Xt           device [N][3] target positions, or NULL: targets = sources (same offsets)
+ *   u, w         device [N][3] outputs (overwritten), same type as the inputs; must not
+ *                overlap any input
+ *   mu, eps      viscosity (> 0) and regularisation (> 0) for every system ...
+ *   eps_per_sys  ... unless non-NULL: host double[n_sys], one eps (> 0) per system
+ *   precision    MRS_F64 | MRS_F32 | MRS_F32_COMP
+ * The first call for a given (offsets, eps, precision, mu) builds a plan (device tables and
+ * scratch) and caches it in the context; later calls with the same shape allocate nothing.
+ * Calls that share a cached plan must not overlap on the GPU (issue them on one stream).
+ * Empty systems are allowed; N = 0 is a no-op.
+ * Errors: MRS_EINVAL (offsets not monotone, eps/mu <= 0, NULL pointers, bad precision),
+ *         MRS_ENOMEM, MRS_ECUDA. */
+MRS_API int mrs_velocity(mrs_ctx* ctx, int n_sys, const int64_t* offsets,
+                 const void* X, const void* f, const void* n, const void* Xt,
+                 void* u, void* w, double mu, double eps, const double* eps_per_sys,
+                 int precision, void* stream);
+
+/* Explicit plans: build once, then execute many times (e.g. inside a CUDA graph).
+ *   config  -1: the library's choice (tuned table or heuristic); otherwise an index into
+ *           mrs_plan_config_count() kernel configurations (tile shape / targets per thread).
+ * A plan owns device tables and scratch; mrs_plan_execute allocates nothing and launches one
+ * persistent kernel (or, for MRS_F64, one plain kernel).  Executions of the same plan must not
+ * overlap on the GPU.  Arguments as for mrs_velocity. */
+MRS_API int mrs_plan_create(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
+                    const double* eps_per_sys, int precision, int config, mrs_plan** plan);
+MRS_API int mrs_plan_execute(mrs_plan* plan, const void* X, const void* f, const void* n,
+                     const void* Xt, void* u, void* w, void* stream);
+MRS_API int mrs_plan_destroy(mrs_plan* plan);
+
+/* Kernel configurations available to plans: count, and a description of entry `config`
+ * (threads per CTA, targets per thread, CTAs resident per SM on this device). */
+MRS_API int mrs_plan_config_count(void);
+MRS_API int mrs_plan_config_info(mrs_ctx* ctx, int config, int* threads, int* targets_per_thread,
+                         int* ctas_per_sm);
+/* Grid size (persistent CTAs) and total work units of a plan, for reporting. */
+MRS_API int mrs_plan_info(const mrs_plan* plan, int* grid, int64_t* work_units, int* config);
+
+/* ==========================================================================================
+ * Kirchhoff rods -- Sections II-A, II-B (Eqs. discrete_f, discrete_n, F_comp_discrete,
+ * N_comp_discrete, mid_triad), Section III-C-1 (rotation square root), Section IV-A
+ * (preferred strain-twist wave).
+ * ========================================================================================== */
+typedef struct {
+    double L;          /* rod length; ds = L/(M-1) for a rod of M nodes */
+    double a[3];       /* bending moduli a1, a2 and torsional rigidity a3 */
+    double b[3];       /* shear moduli b1, b2 and stretching stiffness b3 */
+    double wave_A;     /* amplitude A of Omega_2 = -k^2 A sin(k s + f t) */
+    double wave_k;     /* wavenumber k = 2 pi / lambda */
+    double wave_f;     /* frequency f */
+    double mu;         /* viscosity used by rod_step / parareal_run */
+    double eps;        /* MRS regularisation used by rod_step / parareal_run */
+} mrs_rod_params;
+
+/* Point force g_k and torque m_k that every node applies to the fluid at time t:
+ * g_k = F_{k+1/2} - F_{k-1/2},  m_k = N_{k+1/2} - N_{k-1/2}
+ *        + (1/2)[(X_{k+1}-X_k) x F_{k+1/2} + (X_k-X_{k-1}) x F_{k-1/2}]
+ * (the negatives of the fluid-on-rod densities of Eqs. discrete_f / discrete_n times ds),
+ * with the mid-segment frame D_{k+1/2} = A_k^{1/2} D_k computed in float64 on the GPU.
+ * Free ends: no internal force or moment beyond the first and last node.
+ *   rod_off  host int64[n_rods+1] node offsets; every rod has 2..4096 nodes
+ *   X, D     device float64 [N][3], [N][3][3];  g, m  device float64 [N][3] (outputs)
+ * Errors: MRS_EINVAL, MRS_ECUDA. */
+MRS_API int rod_forces(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_params* p,
+               const double* X, const double* D, double t, double* g, double* m, void* stream);
+
+/* nsteps explicit time steps of all rods as ONE hydrodynamic system (every node is a source
+ * for every node), in place on device float64 X[N][3], D[N][3][3], from time t0 with step dt.
+ * Each stage: rod_forces -> float32 pack -> MRS pair sum (mrs_precision) -> float64 update
+ * (Eq. newx; Eq. newD Rodrigues rotation of the frame by |omega| dt about omega).
+ * scheme MRS_EULER or MRS_RK2 (explicit midpoint on positions and frames).  The steps are
+ * captured once into a CUDA graph per (rods, scheme) and replayed.  Synchronizes `stream`
+ * only at set-up.  Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */
+MRS_API int rod_step(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_params* p,
+             double* X, double* D, double t0, double dt, int nsteps, int scheme,
+             int mrs_precision, void* stream);
+
+/* Principal square root S (S^2 = R, rotation angle halved about the same axis) of n rotation
+ * matrices (Section III-C-1, Eqs. rodrigues / halfangle), float64, device R[n][3][3] ->
+ * S[n][3][3] (row-major).  Computed through the unit quaternion of R and the half-angle
+ * quaternion (1+q)/|1+q|; at an angle of exactly pi either quarter turn is returned.
+ * Errors: MRS_EINVAL, MRS_ECUDA. */
+MRS_API int rot_sqrt_batch(mrs_ctx* ctx, int n, const double* R, double* S, void* stream);
+
+/* ==========================================================================================
+ * Parareal -- Section II-D, Eqs. (initial), (intermediate), (serial_correct); Eq. (true_err).
+ * ========================================================================================== */
+typedef struct {
+    int iterations;          /* Parareal iterations k performed */
+    double incr[64];         /* relative increment eta~^k (Eq. true_err) for k = 1..iterations */
+    double final_incr;       /* eta~ of the last iteration */
+    double seconds;          /* wall time of the call */
+    int64_t fine_steps;      /* fine RK2 steps executed (all slices, all iterations) */
+    int64_t coarse_steps;    /* coarse Euler steps executed */
+} mrs_parareal_stats;
+
+/* Parareal over [T0, T1] split into n_slices equal slices on ONE GPU: coarse G = Euler with
+ * step coarse_ratio*dt_fine, fine F = RK2 with step dt_fine; every iteration runs the fine
+ * solves of all open slices together as independent systems of one batched launch per stage,
+ * then the serial correction X^k_n = F' + G(X^k_{n-1}) - G(X^{k-1}_{n-1}) in float64 with
+ * polar re-orthonormalisation of the frames.  Stops when eta~^k < tol or after max_iter
+ * iterations.  On return X, D (device float64) hold the state at T1.  Synchronizes `stream`.
+ *   out  host, may be NULL.
+ * Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA, MRS_ENOCONV (tolerance not reached within
+ * max_iter, or a non-finite increment; X, D then hold the last iterate). */
+MRS_API int parareal_run(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_params* p,
+                 double* X, double* D, double T0, double T1, int n_slices, double dt_fine,
+                 int coarse_ratio, int max_iter, double tol, mrs_parareal_stats* out,
+                 void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRS_GB300_H */

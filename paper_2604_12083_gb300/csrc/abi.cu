@@ -1,0 +1,410 @@
+// abi.cu -- host side of the C ABI: errors, contexts, pair-sum plans and mrs_velocity.
+#include <cstdarg>
+#include <cmath>
+#include <cstring>
+
+#include "mrs_internal.h"
+
+namespace mrs {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+template <typename T>
+static int dev_alloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return MRS_ENOMEM;
+    }
+    return MRS_OK;
+}
+
+static int check_offsets(int n_sys, const int64_t* off)
+{
+    MRS_REQUIRE(n_sys >= 1, "n_sys must be >= 1 (got %d)", n_sys);
+    MRS_REQUIRE(off != nullptr, "offsets is NULL");
+    MRS_REQUIRE(off[0] == 0, "offsets[0] must be 0 (got %lld)", (long long)off[0]);
+    for (int s = 0; s < n_sys; ++s)
+        MRS_REQUIRE(off[s + 1] >= off[s], "offsets must be non-decreasing (offsets[%d] > offsets[%d])",
+                    s, s + 1);
+    MRS_REQUIRE(off[n_sys] < (int64_t)0x7fffffff, "total points %lld exceed 2^31-1",
+                (long long)off[n_sys]);
+    return MRS_OK;
+}
+
+int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precision)
+{
+    (void)ctx;
+    (void)precision;
+    // Small systems waste lanes in 512-target tiles; use 256-target tiles when most of the
+    // points sit in systems below 4096 points.
+    int64_t small = 0, total = offsets[n_sys];
+    for (int s = 0; s < n_sys; ++s) {
+        const int64_t ns = offsets[s + 1] - offsets[s];
+        if (ns < 4096) small += ns;
+    }
+    if (total > 0 && small * 2 > total) return 1;   // 128 threads x 2 targets
+    return 0;                                        // 128 threads x 4 targets
+}
+
+void plan_free(mrs_plan* p)
+{
+    if (!p) return;
+    cudaFree(p->d_tiles);
+    cudaFree(p->d_sc);
+    cudaFree(p->d_partial);
+    cudaFree(p->d_counters);
+    cudaFree(p->d_off64);
+    cudaFree(p->d_eps64);
+    cudaFree(p->d_tile_sys);
+    cudaFree(p->d_tile_t0);
+    delete p;
+}
+
+int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
+               const double* eps_per_sys, int precision, int config, mrs_plan** out)
+{
+    *out = nullptr;
+    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+    int st = check_offsets(n_sys, offsets);
+    if (st) return st;
+    MRS_REQUIRE(precision == MRS_F64 || precision == MRS_F32 || precision == MRS_F32_COMP,
+                "unknown precision %d", precision);
+    MRS_REQUIRE(std::isfinite(mu) && mu > 0.0, "mu must be > 0 (got %g)", mu);
+    MRS_REQUIRE(config >= -1 && config < kNumConfigs, "config %d out of range", config);
+    std::vector<double> epsv(n_sys);
+    for (int s = 0; s < n_sys; ++s) {
+        epsv[s] = eps_per_sys ? eps_per_sys[s] : eps;
+        MRS_REQUIRE(std::isfinite(epsv[s]) && epsv[s] > 0.0, "eps of system %d must be > 0 (got %g)",
+                    s, epsv[s]);
+    }
+    MRS_CHECK_CUDA(cudaSetDevice(ctx->device));
+
+    mrs_plan* p = new mrs_plan();
+    p->ctx = ctx;
+    p->precision = precision;
+    p->n_sys = n_sys;
+    p->n_points = offsets[n_sys];
+    p->mu = mu;
+    p->offsets.assign(offsets, offsets + n_sys + 1);
+    p->eps = epsv;
+
+    if (precision == MRS_F64) {
+        std::vector<int> bs, bt;
+        for (int s = 0; s < n_sys; ++s)
+            for (int64_t t = offsets[s]; t < offsets[s + 1]; t += kF64Block) {
+                bs.push_back(s);
+                bt.push_back((int)t);
+            }
+        p->n_blocks64 = (int)bs.size();
+        std::vector<long long> off64(offsets, offsets + n_sys + 1);
+        if ((st = dev_alloc(&p->d_off64, off64.size())) || (st = dev_alloc(&p->d_eps64, epsv.size())) ||
+            (st = dev_alloc(&p->d_tile_sys, bs.size())) || (st = dev_alloc(&p->d_tile_t0, bt.size()))) {
+            plan_free(p);
+            return st;
+        }
+        cudaMemcpy(p->d_off64, off64.data(), off64.size() * sizeof(long long), cudaMemcpyHostToDevice);
+        cudaMemcpy(p->d_eps64, epsv.data(), epsv.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (!bs.empty()) {
+            cudaMemcpy(p->d_tile_sys, bs.data(), bs.size() * sizeof(int), cudaMemcpyHostToDevice);
+            cudaMemcpy(p->d_tile_t0, bt.data(), bt.size() * sizeof(int), cudaMemcpyHostToDevice);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            plan_free(p);
+            set_error("plan upload failed: %s", cudaGetErrorString(e));
+            return MRS_ECUDA;
+        }
+        *out = p;
+        return MRS_OK;
+    }
+
+    const int cfg = config >= 0 ? config : default_config(ctx, n_sys, offsets, precision);
+    const KernelConfig kc = kConfigs[cfg];
+    p->config = cfg;
+    p->TM = kc.threads * kc.tpt;
+    std::vector<TileDesc> tiles;
+    long long W = 0;
+    for (int s = 0; s < n_sys; ++s) {
+        const int64_t ns = offsets[s + 1] - offsets[s];
+        if (ns == 0) continue;
+        const int nu = (int)((ns + kUnitSources - 1) / kUnitSources);
+        for (int64_t t = 0; t < ns; t += p->TM) {
+            TileDesc T;
+            T.sys = s;
+            T.t0 = (int)(offsets[s] + t);
+            T.tn = (int)std::min<int64_t>(p->TM, ns - t);
+            T.s0 = (int)offsets[s];
+            T.sn = (int)ns;
+            T.nu = nu;
+            T.u0 = W;
+            tiles.push_back(T);
+            W += nu;
+        }
+    }
+    p->W = W;
+    p->n_tiles = (int)tiles.size();
+    std::vector<SysConst> sc(n_sys);
+    for (int s = 0; s < n_sys; ++s) {
+        const double e2 = epsv[s] * epsv[s];
+        sc[s].e2 = (float)e2;
+        sc[s].c1 = (float)(1.5 * e2);
+        sc[s].c2 = (float)(3.75 * e2 * e2);
+        sc[s].c3 = (float)(-0.75 * e2);
+        sc[s].c5 = (float)(3.75 * e2);
+        sc[s].scale = (float)(1.0 / (8.0 * M_PI * mu));
+    }
+    if (p->n_tiles == 0) {
+        *out = p;
+        return MRS_OK;
+    }
+    int occ = 0;
+    if ((st = occupancy_f32(cfg, precision == MRS_F32_COMP, &occ)) != MRS_OK || occ < 1) {
+        plan_free(p);
+        set_error("occupancy query failed for config %d", cfg);
+        return MRS_ECUDA;
+    }
+    long long P = (long long)ctx->num_sms * occ;
+    if (P > W) P = W;
+    p->P = (int)P;
+    const size_t part_floats = (size_t)2 * P * 12 * p->TM;
+    if ((st = dev_alloc(&p->d_tiles, tiles.size())) || (st = dev_alloc(&p->d_sc, sc.size())) ||
+        (st = dev_alloc(&p->d_partial, part_floats)) || (st = dev_alloc(&p->d_counters, tiles.size()))) {
+        plan_free(p);
+        return st;
+    }
+    cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_sc, sc.data(), sc.size() * sizeof(SysConst), cudaMemcpyHostToDevice);
+    cudaMemset(p->d_counters, 0, tiles.size() * sizeof(int));
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        plan_free(p);
+        set_error("plan upload failed: %s", cudaGetErrorString(e));
+        return MRS_ECUDA;
+    }
+    *out = p;
+    return MRS_OK;
+}
+
+static bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const char* pa = (const char*)a;
+    const char* pb = (const char*)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const void* Xt, void* u,
+             void* w, cudaStream_t s)
+{
+    MRS_REQUIRE(p != nullptr, "plan is NULL");
+    if (p->n_points == 0) return MRS_OK;
+    MRS_REQUIRE(X && f && n && u && w, "NULL input or output pointer");
+    const size_t es = p->precision == MRS_F64 ? 8 : 4;
+    const size_t bytes = (size_t)p->n_points * 3 * es;
+    const void* ins[4] = {X, f, n, Xt ? Xt : X};
+    for (int i = 0; i < 4; ++i)
+        MRS_REQUIRE(!ranges_overlap(ins[i], bytes, u, bytes) && !ranges_overlap(ins[i], bytes, w, bytes),
+                    "outputs must not overlap the inputs");
+    MRS_REQUIRE(!ranges_overlap(u, bytes, w, bytes), "u and w must not overlap");
+    MRS_REQUIRE(((uintptr_t)X | (uintptr_t)f | (uintptr_t)n | (uintptr_t)ins[3] | (uintptr_t)u |
+                 (uintptr_t)w) % es == 0, "pointers must be aligned to the element size");
+    cudaError_t e;
+    if (p->precision == MRS_F64) {
+        MrsLaunch64 L;
+        L.n_sys = p->n_sys;
+        L.offsets = p->d_off64;
+        L.eps = p->d_eps64;
+        L.tile_sys = p->d_tile_sys;
+        L.tile_t0 = p->d_tile_t0;
+        L.n_blocks = p->n_blocks64;
+        L.inv_mu = 1.0 / p->mu;
+        L.X = (const double*)X;
+        L.f = (const double*)f;
+        L.n = (const double*)n;
+        L.Xt = (const double*)ins[3];
+        L.u = (double*)u;
+        L.w = (double*)w;
+        e = launch_mrs_f64(L, s);
+    } else {
+        if (p->n_tiles == 0) return MRS_OK;
+        MrsLaunch L;
+        L.tiles = p->d_tiles;
+        L.n_tiles = p->n_tiles;
+        L.W = p->W;
+        L.P = p->P;
+        L.sc = p->d_sc;
+        L.X = (const float*)X;
+        L.f = (const float*)f;
+        L.n = (const float*)n;
+        L.Xt = (const float*)ins[3];
+        L.u = (float*)u;
+        L.w = (float*)w;
+        L.partial = p->d_partial;
+        L.counters = p->d_counters;
+        e = launch_mrs_f32(p->config, p->precision == MRS_F32_COMP, L, s);
+    }
+    if (e != cudaSuccess) {
+        set_error("pair-sum launch failed: %s", cudaGetErrorString(e));
+        return MRS_ECUDA;
+    }
+    return MRS_OK;
+}
+
+}  // namespace mrs
+
+using namespace mrs;
+
+extern "C" {
+
+const char* mrs_last_error(void) { return g_err; }
+
+const char* mrs_version(void) { return "mrs_gb300 0.1 (sm_103a)"; }
+
+int mrs_ctx_create(mrs_ctx** ctx, int device)
+{
+    clear_error();
+    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+    *ctx = nullptr;
+    int ndev = 0;
+    MRS_CHECK_CUDA(cudaGetDeviceCount(&ndev));
+    MRS_REQUIRE(device >= 0 && device < ndev, "device %d out of range (%d devices)", device, ndev);
+    MRS_CHECK_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    MRS_CHECK_CUDA(cudaGetDeviceProperties(&prop, device));
+    MRS_REQUIRE(prop.major == 10 && prop.minor == 3,
+                "this library is built for sm_103a (GB300); device %d is sm_%d%d", device,
+                prop.major, prop.minor);
+    mrs_ctx* c = new mrs_ctx();
+    c->device = device;
+    c->num_sms = prop.multiProcessorCount;
+    c->cc_major = prop.major;
+    c->cc_minor = prop.minor;
+    c->smem_per_block_optin = prop.sharedMemPerBlockOptin;
+    *ctx = c;
+    return MRS_OK;
+}
+
+int mrs_ctx_destroy(mrs_ctx* ctx)
+{
+    clear_error();
+    if (!ctx) return MRS_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (mrs_plan* p : ctx->plan_cache) plan_free(p);
+    ctx->plan_cache.clear();
+    for (RodWorkspace* w : ctx->rod_ws) rod_ws_free(w);
+    ctx->rod_ws.clear();
+    delete ctx;
+    return MRS_OK;
+}
+
+int mrs_ctx_num_sms(const mrs_ctx* ctx) { return ctx ? ctx->num_sms : 0; }
+
+int mrs_plan_create(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
+                    const double* eps_per_sys, int precision, int config, mrs_plan** plan)
+{
+    clear_error();
+    MRS_REQUIRE(plan != nullptr, "plan is NULL");
+    return plan_build(ctx, n_sys, offsets, mu, eps, eps_per_sys, precision, config, plan);
+}
+
+int mrs_plan_execute(mrs_plan* plan, const void* X, const void* f, const void* n, const void* Xt,
+                     void* u, void* w, void* stream)
+{
+    clear_error();
+    MRS_REQUIRE(plan != nullptr, "plan is NULL");
+    MRS_CHECK_CUDA(cudaSetDevice(plan->ctx->device));
+    return plan_run(plan, X, f, n, Xt, u, w, (cudaStream_t)stream);
+}
+
+int mrs_plan_destroy(mrs_plan* plan)
+{
+    clear_error();
+    if (!plan) return MRS_OK;
+    MRS_REQUIRE(!plan->owned_by_ctx, "plan is owned by its context's cache");
+    cudaSetDevice(plan->ctx->device);
+    plan_free(plan);
+    return MRS_OK;
+}
+
+int mrs_plan_config_count(void) { return kNumConfigs; }
+
+int mrs_plan_config_info(mrs_ctx* ctx, int config, int* threads, int* tpt, int* ctas_per_sm)
+{
+    clear_error();
+    MRS_REQUIRE(config >= 0 && config < kNumConfigs, "config %d out of range", config);
+    if (threads) *threads = kConfigs[config].threads;
+    if (tpt) *tpt = kConfigs[config].tpt;
+    if (ctas_per_sm) {
+        MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+        MRS_CHECK_CUDA(cudaSetDevice(ctx->device));
+        int st = occupancy_f32(config, true, ctas_per_sm);
+        if (st) return st;
+    }
+    return MRS_OK;
+}
+
+int mrs_plan_info(const mrs_plan* plan, int* grid, int64_t* work_units, int* config)
+{
+    clear_error();
+    MRS_REQUIRE(plan != nullptr, "plan is NULL");
+    if (grid) *grid = plan->precision == MRS_F64 ? plan->n_blocks64 : plan->P;
+    if (work_units) *work_units = plan->W;
+    if (config) *config = plan->config;
+    return MRS_OK;
+}
+
+int mrs_velocity(mrs_ctx* ctx, int n_sys, const int64_t* offsets, const void* X, const void* f,
+                 const void* n, const void* Xt, void* u, void* w, double mu, double eps,
+                 const double* eps_per_sys, int precision, void* stream)
+{
+    clear_error();
+    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+    int st = check_offsets(n_sys, offsets);
+    if (st) return st;
+    // look the shape up in the plan cache
+    mrs_plan* hit = nullptr;
+    for (auto it = ctx->plan_cache.begin(); it != ctx->plan_cache.end(); ++it) {
+        mrs_plan* p = *it;
+        if (p->precision != precision || p->n_sys != n_sys || p->mu != mu) continue;
+        if (std::memcmp(p->offsets.data(), offsets, sizeof(int64_t) * (n_sys + 1)) != 0) continue;
+        bool same = true;
+        for (int s = 0; s < n_sys && same; ++s)
+            same = p->eps[s] == (eps_per_sys ? eps_per_sys[s] : eps);
+        if (!same) continue;
+        hit = p;
+        ctx->plan_cache.erase(it);
+        ctx->plan_cache.push_front(hit);
+        break;
+    }
+    if (!hit) {
+        st = plan_build(ctx, n_sys, offsets, mu, eps, eps_per_sys, precision, -1, &hit);
+        if (st) return st;
+        hit->owned_by_ctx = true;
+        ctx->plan_cache.push_front(hit);
+        while (ctx->plan_cache.size() > ctx->plan_cache_max) {  // evict the least recent
+            mrs_plan* old = ctx->plan_cache.back();
+            ctx->plan_cache.pop_back();
+            cudaDeviceSynchronize();   // the evicted plan's scratch may still be in use
+            plan_free(old);
+        }
+    }
+    MRS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    return plan_run(hit, X, f, n, Xt, u, w, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// mrs_internal.h -- internal declarations shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <list>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mrs_gb300.h"
+
+namespace mrs {
+
+// ---------------------------------------------------------------------------------------------
+// Errors: a per-thread message plus the int status of the C ABI.
+// ---------------------------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define MRS_CHECK_CUDA(call)                                                                  \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            ::mrs::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                             __LINE__);                                                       \
+            return MRS_ECUDA;                                                                 \
+        }                                                                                     \
+    } while (0)
+
+#define MRS_REQUIRE(cond, ...)                  \
+    do {                                        \
+        if (!(cond)) {                          \
+            ::mrs::set_error(__VA_ARGS__);      \
+            return MRS_EINVAL;                  \
+        }                                       \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// Pair-sum work description (float32 persistent kernel).
+//
+// A system's targets are cut into tiles of TM = threads * targets_per_thread targets.  Each
+// tile sweeps all sources of its system; that sweep is cut into work units of kUnitSources
+// sources.  The units of all tiles are numbered consecutively (tile by tile) and CTA p of the
+// persistent grid of P CTAs processes units [W p / P, W (p+1) / P): every CTA gets the same
+// number of pairs up to one unit, whatever the mix of system sizes.  A tile processed by more
+// than one CTA is completed by whichever of them finishes last (an atomic unit counter per
+// tile), which sums the partial results in a fixed order.
+// ---------------------------------------------------------------------------------------------
+constexpr int kUnitSources = 32;   // sources per work unit (granularity of the CTA ranges)
+constexpr int kChunk = 256;        // sources staged in shared memory at a time
+
+struct TileDesc {
+    int sys;     // system index
+    int t0;      // first target (global point index)
+    int tn;      // number of targets in the tile (1..TM)
+    int s0;      // first source of the system (global point index)
+    int sn;      // number of sources of the system
+    int nu;      // number of work units = ceil(sn / kUnitSources)
+    long long u0;  // global index of the tile's first unit
+};
+
+struct SysConst {  // per-system constants of the scaled kernels (see mrs_kernels.cu)
+    float e2, c1, c2, c3, c5, scale;
+};
+
+struct KernelConfig {
+    int threads;   // threads per CTA
+    int tpt;       // targets per thread
+};
+
+// Configurations compiled into the library (index = plan config id).
+extern const KernelConfig kConfigs[];
+extern const int kNumConfigs;
+
+struct MrsLaunch {
+    const TileDesc* tiles;
+    int n_tiles;
+    long long W;          // total work units
+    int P;                // persistent CTAs
+    const SysConst* sc;
+    const float* X;
+    const float* f;
+    const float* n;
+    const float* Xt;      // targets (== X when none given)
+    float* u;
+    float* w;
+    float* partial;       // [2P][12][TM] floats
+    int* counters;        // [n_tiles], zero between launches
+};
+
+cudaError_t launch_mrs_f32(int config, bool comp, const MrsLaunch& L, cudaStream_t s);
+int occupancy_f32(int config, bool comp, int* ctas_per_sm);
+
+struct MrsLaunch64 {
+    int n_sys;
+    const long long* offsets;   // device [n_sys+1]
+    const double* eps;          // device [n_sys]
+    const int* tile_sys;        // device [n_blocks]: system of each 128-target block
+    const int* tile_t0;         // device [n_blocks]: first target of each block
+    int n_blocks;
+    double inv_mu;
+    const double* X;
+    const double* f;
+    const double* n;
+    const double* Xt;
+    double* u;
+    double* w;
+};
+cudaError_t launch_mrs_f64(const MrsLaunch64& L, cudaStream_t s);
+constexpr int kF64Block = 128;
+
+struct RodWorkspace;
+void rod_ws_free(RodWorkspace* ws);
+
+}  // namespace mrs
+
+// ---------------------------------------------------------------------------------------------
+// Opaque ABI objects.
+// ---------------------------------------------------------------------------------------------
+struct mrs_plan {
+    mrs_ctx* ctx = nullptr;
+    int precision = MRS_F32_COMP;
+    int config = 0;
+    int n_sys = 0;
+    int64_t n_points = 0;
+    double mu = 1.0;
+    std::vector<int64_t> offsets;
+    std::vector<double> eps;
+    // float32 persistent path
+    int P = 0;
+    int TM = 0;
+    long long W = 0;
+    int n_tiles = 0;
+    mrs::TileDesc* d_tiles = nullptr;
+    mrs::SysConst* d_sc = nullptr;
+    float* d_partial = nullptr;
+    int* d_counters = nullptr;
+    // float64 path
+    long long* d_off64 = nullptr;
+    double* d_eps64 = nullptr;
+    int* d_tile_sys = nullptr;
+    int* d_tile_t0 = nullptr;
+    int n_blocks64 = 0;
+    bool owned_by_ctx = false;
+};
+
+struct mrs_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t smem_per_block_optin = 0;
+    // plan cache used by mrs_velocity (LRU, most recent first)
+    std::list<mrs_plan*> plan_cache;
+    size_t plan_cache_max = 16;
+    // rod workspaces used by rod_forces / rod_step / parareal_run (LRU, most recent first)
+    std::list<mrs::RodWorkspace*> rod_ws;
+    size_t rod_ws_max = 96;
+};
+
+namespace mrs {
+int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
+               const double* eps_per_sys, int precision, int config, mrs_plan** out);
+int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const void* Xt, void* u,
+             void* w, cudaStream_t s);
+void plan_free(mrs_plan* p);
+int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precision);
+}  // namespace mrs

@@ -1,0 +1,432 @@
+// mrs_kernels.cu -- the regularized-Stokeslet pair sum on sm_103a.
+//
+// Section II-C, Eqs. (velocity_field), (angular_velocity_field), (superposition); Section
+// III-C-2.  For every target i and every source j of its system (self pair included):
+//   mu u_i     += f_j H1 + (f_j.r) r H2 + (n_j x r) H3
+//   mu omega_i += (f_j x r) H3 + n_j H4 + (n_j.r) r H5,         r = x_i - X_j.
+//
+// Arithmetic.  With d = r^2 + eps^2, s = d^{-1/2} (SFU rsqrt), s2 = 1/d (SFU rcp), s3 = s s2,
+// s5 = s3 s2 and e2 = eps^2, the identity d s2 = 1 turns every polynomial in r^2 = d - e2 of
+// the kernels into one in s2:
+//   8 pi H1 = s + e2 s3                      8 pi H2 = s3
+//   8 pi H3 = s3 + (3/2) e2 s5               8 pi H5 = s5 (3/2 + (15/4) e2 s2)
+//   8 pi H4 = s3 (-1/2 + s2 (-(3/4) e2 + (15/4) e2^2 s2))
+// so one pair costs 53 FP32 instructions (FFMA/FMUL/FADD) and 2 SFU instructions, and the
+// common factor 1/(8 pi mu) is applied once per target.  No tensor cores: the pair sum is not
+// a dense contraction.
+//
+// Float32 path (MRS_F32 / MRS_F32_COMP): one persistent kernel over all systems of a batch.
+//   * CTA p of P processes the contiguous range [W p/P, W (p+1)/P) of the W work units (a
+//     unit = one target tile x kUnitSources sources), so every CTA gets the same number of
+//     pairs whatever the system sizes (no tail of idle SMs).
+//   * Each thread holds TPT targets in registers (targets tid, tid+BLOCK, ... of the tile);
+//     sources are staged kChunk at a time in shared memory as three float4 per source and read
+//     by warp-wide broadcast, so each shared load is reused TPT times.
+//   * Accumulation: per-chunk float32 partials; in MRS_F32_COMP each chunk's partial is folded
+//     into a per-target Kahan pair (sum, compensation) held in shared memory.
+//   * A tile whose units are spread over several CTAs: each CTA writes its partial to its own
+//     scratch slot, then adds its unit count to the tile's counter; the CTA that completes the
+//     count sums all slots in CTA order (float64) and writes the result, then zeroes the
+//     counter for the next launch.  No CTA ever waits for another.
+//
+// Float64 path (MRS_F64): one CTA per 128 targets, all sources of the system staged through
+// shared memory, float64 arithmetic with the kernels written in r^2.
+#include "mrs_internal.h"
+
+namespace mrs {
+
+__device__ __forceinline__ float sfu_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sfu_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// One (target, source) pair accumulated into acc[0..2] (u) and acc[3..5] (omega), both scaled
+// by 8 pi mu.  a = (X.x, X.y, X.z, f.x), b = (f.y, f.z, n.x, n.y), nz = n.z.
+__device__ __forceinline__ void pair_f32(float xi, float yi, float zi, const float4 a,
+                                         const float4 b, float nz, float e2, float c1, float c2,
+                                         float c3, float c5, float* acc)
+{
+    const float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
+    const float fx = a.w, fy = b.x, fz = b.y, nx = b.z, ny = b.w;
+    const float d = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, e2)));
+    const float s = sfu_rsqrt(d);
+    const float s2 = sfu_rcp(d);
+    const float s3 = s * s2;
+    const float s5 = s3 * s2;
+    const float h1 = fmaf(e2, s3, s);                        // 8 pi H1
+    const float h3 = fmaf(c1, s5, s3);                       // 8 pi H3
+    const float h4 = s3 * fmaf(s2, fmaf(c2, s2, c3), -0.5f);  // 8 pi H4
+    const float h5 = s5 * fmaf(c5, s2, 1.5f);                // 8 pi H5
+    const float fr = fmaf(fx, rx, fmaf(fy, ry, fz * rz));
+    const float nr = fmaf(nx, rx, fmaf(ny, ry, nz * rz));
+    const float bf = s3 * fr;                                // 8 pi H2 (f.r)
+    const float bn = h5 * nr;                                // 8 pi H5 (n.r)
+    // u += H1 f + H2 (f.r) r + H3 (n x r)
+    const float hnx = h3 * nx, hny = h3 * ny, hnz = h3 * nz;
+    acc[0] = fmaf(h1, fx, acc[0]);
+    acc[1] = fmaf(h1, fy, acc[1]);
+    acc[2] = fmaf(h1, fz, acc[2]);
+    acc[0] = fmaf(bf, rx, acc[0]);
+    acc[1] = fmaf(bf, ry, acc[1]);
+    acc[2] = fmaf(bf, rz, acc[2]);
+    acc[0] = fmaf(hny, rz, acc[0]);
+    acc[1] = fmaf(hnz, rx, acc[1]);
+    acc[2] = fmaf(hnx, ry, acc[2]);
+    acc[0] = fmaf(-hnz, ry, acc[0]);
+    acc[1] = fmaf(-hnx, rz, acc[1]);
+    acc[2] = fmaf(-hny, rx, acc[2]);
+    // omega += H3 (f x r) + H4 n + H5 (n.r) r
+    const float hfx = h3 * fx, hfy = h3 * fy, hfz = h3 * fz;
+    acc[3] = fmaf(h4, nx, acc[3]);
+    acc[4] = fmaf(h4, ny, acc[4]);
+    acc[5] = fmaf(h4, nz, acc[5]);
+    acc[3] = fmaf(bn, rx, acc[3]);
+    acc[4] = fmaf(bn, ry, acc[4]);
+    acc[5] = fmaf(bn, rz, acc[5]);
+    acc[3] = fmaf(hfy, rz, acc[3]);
+    acc[4] = fmaf(hfz, rx, acc[4]);
+    acc[5] = fmaf(hfx, ry, acc[5]);
+    acc[3] = fmaf(-hfz, ry, acc[3]);
+    acc[4] = fmaf(-hfx, rz, acc[4]);
+    acc[5] = fmaf(-hfy, rx, acc[5]);
+}
+
+__device__ __forceinline__ long long unit_start(long long W, int P, int p)
+{
+    return (W * (long long)p) / (long long)P;
+}
+
+// The CTA whose unit range contains unit x.
+__device__ __forceinline__ int cta_of_unit(long long W, int P, long long x)
+{
+    int q = (int)((x * (long long)P) / W);
+    if (q > P - 1) q = P - 1;
+    while (q + 1 < P && unit_start(W, P, q + 1) <= x) ++q;
+    while (q > 0 && unit_start(W, P, q) > x) --q;
+    return q;
+}
+
+template <int BLOCK>
+struct MinBlocks {
+    static constexpr int value = BLOCK >= 256 ? 2 : (BLOCK >= 128 ? 4 : 8);
+};
+
+template <int BLOCK, int TPT, bool COMP>
+__global__ void __launch_bounds__(BLOCK, MinBlocks<BLOCK>::value)
+mrs_f32_persistent(const MrsLaunch L)
+{
+    constexpr int TM = BLOCK * TPT;
+    __shared__ __align__(16) float sflat[kChunk * 12];
+    __shared__ float2 kah[COMP ? 6 * TPT * BLOCK : 1];
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x;
+    const int p = blockIdx.x;
+    long long ubeg = unit_start(L.W, L.P, p);
+    const long long uend = unit_start(L.W, L.P, p + 1);
+    if (ubeg >= uend) return;
+
+    // lanes 9..11 of every staged source stay zero
+    for (int i = tid; i < kChunk; i += BLOCK) {
+        sflat[i * 12 + 9] = 0.f;
+        sflat[i * 12 + 10] = 0.f;
+        sflat[i * 12 + 11] = 0.f;
+    }
+    // first tile: the last one whose first unit is <= ubeg
+    int ti;
+    {
+        int lo = 0, hi = L.n_tiles - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.tiles[mid].u0 <= ubeg) lo = mid; else hi = mid - 1;
+        }
+        ti = lo;
+    }
+    bool first_seg = true;
+
+    while (ubeg < uend) {
+        const TileDesc T = L.tiles[ti];
+        const long long send = min(uend, T.u0 + (long long)T.nu);
+        const int ua = (int)(ubeg - T.u0), ub = (int)(send - T.u0);
+        const bool full = (ua == 0 && ub == T.nu);
+        const SysConst sc = L.sc[T.sys];
+
+        float xt[TPT][3];
+        float acc[TPT][6];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            const int li = k * BLOCK + tid;
+            const long long gi = (long long)T.t0 + (li < T.tn ? li : T.tn - 1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) xt[k][c] = L.Xt[gi * 3 + c];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc[k][q] = 0.f;
+            if (COMP) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) kah[(q * TPT + k) * BLOCK + tid] = make_float2(0.f, 0.f);
+            }
+        }
+
+        const long long jbeg = (long long)T.s0 + (long long)ua * kUnitSources;
+        const long long jend = (long long)T.s0 + min((long long)ub * kUnitSources, (long long)T.sn);
+        for (long long j0 = jbeg; j0 < jend; j0 += kChunk) {
+            const int cnt = (int)min((long long)kChunk, jend - j0);
+            const int cntp = (cnt + 3) & ~3;
+            __syncthreads();  // the previous chunk is no longer read
+            const float* gX = L.X + j0 * 3;
+            const float* gf = L.f + j0 * 3;
+            const float* gn = L.n + j0 * 3;
+            for (int idx = tid; idx < cnt * 3; idx += BLOCK) {
+                const int sidx = idx / 3, c = idx - sidx * 3;
+                sflat[sidx * 12 + c] = __ldg(gX + idx);
+                sflat[sidx * 12 + 3 + c] = __ldg(gf + idx);
+                sflat[sidx * 12 + 6 + c] = __ldg(gn + idx);
+            }
+            for (int sidx = cnt + tid; sidx < cntp; sidx += BLOCK) {
+#pragma unroll
+                for (int c = 0; c < 9; ++c) sflat[sidx * 12 + c] = 0.f;  // zero source: adds 0
+            }
+            __syncthreads();
+
+            const float e2 = sc.e2, c1 = sc.c1, c2 = sc.c2, c3 = sc.c3, c5 = sc.c5;
+#pragma unroll 2
+            for (int j = 0; j < cntp; ++j) {
+                const float4 a = *reinterpret_cast<const float4*>(&sflat[j * 12]);
+                const float4 b = *reinterpret_cast<const float4*>(&sflat[j * 12 + 4]);
+                const float nz = sflat[j * 12 + 8];
+#pragma unroll
+                for (int k = 0; k < TPT; ++k)
+                    pair_f32(xt[k][0], xt[k][1], xt[k][2], a, b, nz, e2, c1, c2, c3, c5, acc[k]);
+            }
+            if (COMP) {
+                // Kahan fold of this chunk's partial into (sum, compensation)
+#pragma unroll
+                for (int k = 0; k < TPT; ++k) {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        float2 sc2 = kah[(q * TPT + k) * BLOCK + tid];
+                        const float y = __fsub_rn(acc[k][q], sc2.y);
+                        const float t = __fadd_rn(sc2.x, y);
+                        sc2.y = __fsub_rn(__fsub_rn(t, sc2.x), y);
+                        sc2.x = t;
+                        kah[(q * TPT + k) * BLOCK + tid] = sc2;
+                        acc[k][q] = 0.f;
+                    }
+                }
+            }
+        }
+
+        // --- result of this segment -------------------------------------------------------
+        if (full) {
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                const int li = k * BLOCK + tid;
+                if (li < T.tn) {
+                    const long long gi = (long long)T.t0 + li;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        float v;
+                        if (COMP) {
+                            const float2 sc2 = kah[(q * TPT + k) * BLOCK + tid];
+                            v = (float)((double)sc2.x - (double)sc2.y);
+                        } else {
+                            v = acc[k][q];
+                        }
+                        v *= sc.scale;
+                        if (q < 3) L.u[gi * 3 + q] = v; else L.w[gi * 3 + q - 3] = v;
+                    }
+                }
+            }
+        } else {
+            const int slot = 2 * p + (first_seg ? 0 : 1);
+            float* part = L.partial + (size_t)slot * 12 * TM;
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                const int li = k * BLOCK + tid;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    if (COMP) {
+                        const float2 sc2 = kah[(q * TPT + k) * BLOCK + tid];
+                        part[q * TM + li] = sc2.x;
+                        part[(6 + q) * TM + li] = sc2.y;
+                    } else {
+                        part[q * TM + li] = acc[k][q];
+                    }
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                const int mine = ub - ua;
+                const int old = atomicAdd(&L.counters[ti], mine);
+                s_last = (old + mine == T.nu) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                const int q_lo = cta_of_unit(L.W, L.P, T.u0);
+                const int q_hi = cta_of_unit(L.W, L.P, T.u0 + T.nu - 1);
+                double tot[TPT][6];
+#pragma unroll
+                for (int k = 0; k < TPT; ++k)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) tot[k][q] = 0.0;
+                for (int qc = q_lo; qc <= q_hi; ++qc) {
+                    const long long st = unit_start(L.W, L.P, qc);
+                    if (st == unit_start(L.W, L.P, qc + 1)) continue;   // empty CTA range
+                    const int sl = 2 * qc + (st < T.u0 ? 1 : 0);
+                    const float* pp = L.partial + (size_t)sl * 12 * TM;
+#pragma unroll
+                    for (int k = 0; k < TPT; ++k) {
+                        const int li = k * BLOCK + tid;
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) {
+                            double v = (double)__ldcg(pp + q * TM + li);
+                            if (COMP) v -= (double)__ldcg(pp + (6 + q) * TM + li);
+                            tot[k][q] += v;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < TPT; ++k) {
+                    const int li = k * BLOCK + tid;
+                    if (li < T.tn) {
+                        const long long gi = (long long)T.t0 + li;
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) {
+                            const float v = (float)tot[k][q] * sc.scale;
+                            if (q < 3) L.u[gi * 3 + q] = v; else L.w[gi * 3 + q - 3] = v;
+                        }
+                    }
+                }
+                if (tid == 0) L.counters[ti] = 0;
+            }
+        }
+        first_seg = false;
+        ubeg = send;
+        ++ti;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Configuration table and dispatch.
+// ---------------------------------------------------------------------------------------------
+const KernelConfig kConfigs[] = {
+    {128, 4}, {128, 2}, {128, 8}, {64, 4}, {256, 2}, {128, 1},
+};
+const int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
+
+template <int BLOCK, int TPT, bool COMP>
+static cudaError_t launch_t(const MrsLaunch& L, cudaStream_t s)
+{
+    mrs_f32_persistent<BLOCK, TPT, COMP><<<L.P, BLOCK, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+template <int BLOCK, int TPT, bool COMP>
+static int occ_t(int* n)
+{
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        n, mrs_f32_persistent<BLOCK, TPT, COMP>, BLOCK, 0);
+    return e == cudaSuccess ? MRS_OK : MRS_ECUDA;
+}
+
+#define MRS_DISPATCH(cfg, comp, FN, ...)                                                    \
+    switch (cfg) {                                                                          \
+    case 0: return comp ? FN<128, 4, true>(__VA_ARGS__) : FN<128, 4, false>(__VA_ARGS__);   \
+    case 1: return comp ? FN<128, 2, true>(__VA_ARGS__) : FN<128, 2, false>(__VA_ARGS__);   \
+    case 2: return comp ? FN<128, 8, true>(__VA_ARGS__) : FN<128, 8, false>(__VA_ARGS__);   \
+    case 3: return comp ? FN<64, 4, true>(__VA_ARGS__) : FN<64, 4, false>(__VA_ARGS__);     \
+    case 4: return comp ? FN<256, 2, true>(__VA_ARGS__) : FN<256, 2, false>(__VA_ARGS__);   \
+    case 5: return comp ? FN<128, 1, true>(__VA_ARGS__) : FN<128, 1, false>(__VA_ARGS__);   \
+    default: break;                                                                         \
+    }
+
+cudaError_t launch_mrs_f32(int config, bool comp, const MrsLaunch& L, cudaStream_t s)
+{
+    MRS_DISPATCH(config, comp, launch_t, L, s);
+    return cudaErrorInvalidValue;
+}
+
+int occupancy_f32(int config, bool comp, int* ctas_per_sm)
+{
+    MRS_DISPATCH(config, comp, occ_t, ctas_per_sm);
+    return MRS_EINVAL;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Float64 kernel.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kF64Block) mrs_f64_kernel(const MrsLaunch64 L)
+{
+    __shared__ double sx[kF64Block * 9];
+    const int b = blockIdx.x;
+    const int sys = L.tile_sys[b];
+    const long long s0 = L.offsets[sys], s1 = L.offsets[sys + 1];
+    const long long i = (long long)L.tile_t0[b] + threadIdx.x;
+    const bool valid = i < s1;
+    const long long ii = valid ? i : s1 - 1;
+    const double xi = L.Xt[ii * 3 + 0], yi = L.Xt[ii * 3 + 1], zi = L.Xt[ii * 3 + 2];
+    const double e2 = L.eps[sys] * L.eps[sys];
+    double u0 = 0, u1 = 0, u2 = 0, w0 = 0, w1 = 0, w2 = 0;
+    for (long long j0 = s0; j0 < s1; j0 += kF64Block) {
+        const int cnt = (int)min((long long)kF64Block, s1 - j0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < cnt * 3; idx += kF64Block) {
+            const int sidx = idx / 3, c = idx - sidx * 3;
+            sx[sidx * 9 + c] = L.X[j0 * 3 + idx];
+            sx[sidx * 9 + 3 + c] = L.f[j0 * 3 + idx];
+            sx[sidx * 9 + 6 + c] = L.n[j0 * 3 + idx];
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            const double* q = sx + j * 9;
+            const double rx = xi - q[0], ry = yi - q[1], rz = zi - q[2];
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            const double s = rsqrt(r2 + e2);
+            const double s2 = s * s, s3 = s2 * s, s5 = s3 * s2, s7 = s5 * s2;
+            // 8 pi H1..H5
+            const double h1 = (r2 + 2.0 * e2) * s3;
+            const double h2 = s3;
+            const double h3 = 0.5 * (2.0 * r2 + 5.0 * e2) * s5;
+            const double h4 = 0.25 * (10.0 * e2 * e2 - 7.0 * e2 * r2 - 2.0 * r2 * r2) * s7;
+            const double h5 = 0.25 * (6.0 * r2 + 21.0 * e2) * s7;
+            const double fx = q[3], fy = q[4], fz = q[5], nx = q[6], ny = q[7], nz = q[8];
+            const double fr = fx * rx + fy * ry + fz * rz;
+            const double nr = nx * rx + ny * ry + nz * rz;
+            u0 += h1 * fx + h2 * fr * rx + h3 * (ny * rz - nz * ry);
+            u1 += h1 * fy + h2 * fr * ry + h3 * (nz * rx - nx * rz);
+            u2 += h1 * fz + h2 * fr * rz + h3 * (nx * ry - ny * rx);
+            w0 += h3 * (fy * rz - fz * ry) + h4 * nx + h5 * nr * rx;
+            w1 += h3 * (fz * rx - fx * rz) + h4 * ny + h5 * nr * ry;
+            w2 += h3 * (fx * ry - fy * rx) + h4 * nz + h5 * nr * rz;
+        }
+    }
+    if (valid) {
+        const double sc = L.inv_mu / (8.0 * 3.14159265358979323846);
+        L.u[i * 3 + 0] = u0 * sc;
+        L.u[i * 3 + 1] = u1 * sc;
+        L.u[i * 3 + 2] = u2 * sc;
+        L.w[i * 3 + 0] = w0 * sc;
+        L.w[i * 3 + 1] = w1 * sc;
+        L.w[i * 3 + 2] = w2 * sc;
+    }
+}
+
+cudaError_t launch_mrs_f64(const MrsLaunch64& L, cudaStream_t s)
+{
+    if (L.n_blocks == 0) return cudaSuccess;
+    mrs_f64_kernel<<<L.n_blocks, kF64Block, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace mrs

@@ -1,0 +1,79 @@
+// rod_internal.h -- rod kernels, rod workspaces (device buffers + captured step graphs).
+#pragma once
+
+#include "mrs_internal.h"
+
+namespace mrs {
+
+struct RodLaunch {
+    int N;                     // nodes in the batch (all instances)
+    int nodes_per_inst;        // nodes of one instance
+    const int2* node_info;     // [N]: (index within rod, nodes of the rod)
+    const double* t0;          // [n_inst]: start time of every instance
+    long long* step;           // step counter of the current run (time = t0 + step * dt)
+    double dt;
+    mrs_rod_params p;
+    double* FN;                // [N][6] segment force / moment scratch
+};
+
+cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double* D, double t_off,
+                              double* g64, double* m64, float* Xf, float* gf, float* mf,
+                              cudaStream_t s);
+cudaError_t launch_rod_update(const RodLaunch& L, const double* X0, const double* D0,
+                              const float* u, const float* w, double h, double* X1, double* D1,
+                              bool bump_step, cudaStream_t s);
+cudaError_t launch_rod_update64(const RodLaunch& L, const double* X0, const double* D0,
+                                const double* u, const double* w, double h, double* X1,
+                                double* D1, bool bump_step, cudaStream_t s);
+cudaError_t launch_rot_sqrt_batch(int n, const double* R, double* S, cudaStream_t s);
+
+// One batch of n_inst identical rod sets (instance i = the rods of rod_off shifted by i*N1
+// nodes); every instance is its own hydrodynamic system.
+struct RodWorkspace {
+    mrs_ctx* ctx = nullptr;
+    int n_inst = 0;
+    int n_rods = 0;            // rods per instance
+    int N1 = 0;                // nodes per instance
+    int N = 0;                 // total nodes
+    int precision = MRS_F32_COMP;
+    std::vector<int64_t> rod_off;   // per instance, n_rods+1
+    int2* d_node_info = nullptr;
+    double* d_t0 = nullptr;
+    long long* d_step = nullptr;
+    double* d_FN = nullptr;
+    float* d_Xf = nullptr;
+    float* d_gf = nullptr;
+    float* d_mf = nullptr;
+    float* d_u = nullptr;
+    float* d_w = nullptr;
+    double* d_g64 = nullptr;
+    double* d_m64 = nullptr;
+    double* d_u64 = nullptr;
+    double* d_w64 = nullptr;
+    double* d_Xh = nullptr;
+    double* d_Dh = nullptr;
+    mrs_plan* plan = nullptr;
+    cudaStream_t cap = nullptr;   // private stream used only for graph capture
+    struct Graph {
+        const double* X;
+        const double* D;
+        int scheme;
+        int steps;
+        double dt;
+        mrs_rod_params p;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+};
+
+int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int precision,
+               double mu, double eps, RodWorkspace** out);
+void rod_ws_free(RodWorkspace* ws);
+RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt);
+// Enqueue `nsteps` steps of size dt on the workspace's state buffers X, D (device), with the
+// instance start times already set; replays captured graphs.
+int rod_ws_steps(RodWorkspace* ws, const mrs_rod_params* p, double* X, double* D, double dt,
+                 int nsteps, int scheme, cudaStream_t s);
+int rod_ws_set_times(RodWorkspace* ws, const double* t0_host, cudaStream_t s);
+
+}  // namespace mrs

@@ -1,0 +1,282 @@
+// rod_kernels.cu -- float64 Kirchhoff-rod kernels on sm_103a.
+//
+// Sections II-A, II-B: Eqs. (discrete_f), (discrete_n), (F_comp_discrete), (N_comp_discrete),
+// (mid_triad); Section III-C-1 (rotation square root); Section III-C-3: Eqs. (newx), (newD);
+// Section IV-A (preferred strain-twist wave).
+//
+// Layout: node k of the whole batch (all instances, all rods) is one row; X[k*3+c],
+// D[k*9 + i*3 + c] (row i = director D^{i+1}).  node_info[k] = (index of k within its rod,
+// number of nodes of its rod); segment k+1/2 exists when the index is below M-1 and is
+// stored at row k of the segment buffer FN (F_{k+1/2} then N_{k+1/2}, 6 doubles).
+//
+// Mid-segment frame: A_k = D_{k+1}^T D_k (= sum_j D^j_{k+1} (D^j_k)^T) is turned into its unit
+// quaternion q (Shepperd's pivoted formula), the principal square root is the quaternion
+// (1 + q)/|1 + q| (q taken with a non-negative scalar part), and each director of D_k is
+// rotated by it.  This is the same principal root as the half-angle Rodrigues form of the
+// paper, reached without trigonometric calls or endpoint branches.
+#include <cmath>
+
+#include "rod_internal.h"
+
+namespace mrs {
+
+__device__ __forceinline__ double dot3(const double* a, const double* b)
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Unit quaternion (w, x, y, z) of a rotation matrix A (row-major), w >= 0.
+__device__ __forceinline__ void rot_to_quat(const double* A, double* q)
+{
+    const double tr = A[0] + A[4] + A[8];
+    if (tr >= A[0] && tr >= A[4] && tr >= A[8]) {
+        const double r = sqrt(fmax(1.0 + tr, 0.0));
+        const double s = 0.5 / r;
+        q[0] = 0.5 * r;
+        q[1] = (A[7] - A[5]) * s;
+        q[2] = (A[2] - A[6]) * s;
+        q[3] = (A[3] - A[1]) * s;
+    } else if (A[0] >= A[4] && A[0] >= A[8]) {
+        const double r = sqrt(fmax(1.0 + A[0] - A[4] - A[8], 0.0));
+        const double s = 0.5 / r;
+        q[1] = 0.5 * r;
+        q[0] = (A[7] - A[5]) * s;
+        q[2] = (A[1] + A[3]) * s;
+        q[3] = (A[2] + A[6]) * s;
+    } else if (A[4] >= A[8]) {
+        const double r = sqrt(fmax(1.0 - A[0] + A[4] - A[8], 0.0));
+        const double s = 0.5 / r;
+        q[2] = 0.5 * r;
+        q[0] = (A[2] - A[6]) * s;
+        q[1] = (A[1] + A[3]) * s;
+        q[3] = (A[5] + A[7]) * s;
+    } else {
+        const double r = sqrt(fmax(1.0 - A[0] - A[4] + A[8], 0.0));
+        const double s = 0.5 / r;
+        q[3] = 0.5 * r;
+        q[0] = (A[3] - A[1]) * s;
+        q[1] = (A[2] + A[6]) * s;
+        q[2] = (A[5] + A[7]) * s;
+    }
+    if (q[0] < 0.0) {
+        q[0] = -q[0];
+        q[1] = -q[1];
+        q[2] = -q[2];
+        q[3] = -q[3];
+    }
+    const double nn = rsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    q[0] *= nn;
+    q[1] *= nn;
+    q[2] *= nn;
+    q[3] *= nn;
+}
+
+// Rotation matrix (row-major) of the principal square root of the rotation A.
+__device__ void rot_sqrt_dev(const double* A, double* S)
+{
+    double q[4];
+    rot_to_quat(A, q);
+    // half-angle quaternion: (1 + q) / |1 + q|, |1 + q|^2 = 2 (1 + w)
+    const double inv = rsqrt(2.0 * (1.0 + q[0]));
+    const double a = (1.0 + q[0]) * inv, b = q[1] * inv, c = q[2] * inv, d = q[3] * inv;
+    S[0] = 1.0 - 2.0 * (c * c + d * d);
+    S[1] = 2.0 * (b * c - a * d);
+    S[2] = 2.0 * (b * d + a * c);
+    S[3] = 2.0 * (b * c + a * d);
+    S[4] = 1.0 - 2.0 * (b * b + d * d);
+    S[5] = 2.0 * (c * d - a * b);
+    S[6] = 2.0 * (b * d - a * c);
+    S[7] = 2.0 * (c * d + a * b);
+    S[8] = 1.0 - 2.0 * (b * b + c * c);
+}
+
+__global__ void rot_sqrt_batch_kernel(int n, const double* R, double* S)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rot_sqrt_dev(R + 9 * (size_t)i, S + 9 * (size_t)i);
+}
+
+// Segment k+1/2: internal force F and moment N in lab coordinates (Eqs. mid_triad,
+// F_comp_discrete, N_comp_discrete; Omega of Section IV-A at the segment midpoint).
+__global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__ X,
+                                   const double* __restrict__ D, double t_off)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.N) return;
+    const int2 ni = L.node_info[k];
+    if (ni.x >= ni.y - 1) return;  // last node of its rod: no segment
+    const double ds = L.p.L / (double)(ni.y - 1);
+    const int inst = k / L.nodes_per_inst;
+    const double t = L.t0[inst] + (double)(*L.step) * L.dt + t_off;
+    const double* Dk = D + 9 * (size_t)k;
+    const double* Dk1 = Dk + 9;
+    double A[9], S[9], Dh[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            A[3 * r + c] = Dk1[r] * Dk[c] + Dk1[3 + r] * Dk[3 + c] + Dk1[6 + r] * Dk[6 + c];
+    rot_sqrt_dev(A, S);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            Dh[3 * i + r] = S[3 * r] * Dk[3 * i] + S[3 * r + 1] * Dk[3 * i + 1] + S[3 * r + 2] * Dk[3 * i + 2];
+    const double* Xk = X + 3 * (size_t)k;
+    const double e[3] = {(Xk[3] - Xk[0]) / ds, (Xk[4] - Xk[1]) / ds, (Xk[5] - Xk[2]) / ds};
+    const double s_mid = ((double)ni.x + 0.5) * ds;
+    const double om2 = -L.p.wave_k * L.p.wave_k * L.p.wave_A * sin(L.p.wave_k * s_mid + L.p.wave_f * t);
+    double F[3] = {0, 0, 0}, Nm[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double Fi = L.p.b[i] * (dot3(e, Dh + 3 * i) - (i == 2 ? 1.0 : 0.0));
+        const int j = (i + 1) % 3, l = (i + 2) % 3;
+        const double dD[3] = {(Dk1[3 * j] - Dk[3 * j]) / ds, (Dk1[3 * j + 1] - Dk[3 * j + 1]) / ds,
+                              (Dk1[3 * j + 2] - Dk[3 * j + 2]) / ds};
+        const double Ni = L.p.a[i] * (dot3(dD, Dh + 3 * l) - (i == 1 ? om2 : 0.0));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            F[c] += Fi * Dh[3 * i + c];
+            Nm[c] += Ni * Dh[3 * i + c];
+        }
+    }
+    double* o = L.FN + 6 * (size_t)k;
+    o[0] = F[0];
+    o[1] = F[1];
+    o[2] = F[2];
+    o[3] = Nm[0];
+    o[4] = Nm[1];
+    o[5] = Nm[2];
+}
+
+// Node k: g_k = F_{k+1/2} - F_{k-1/2}, m_k = N_{k+1/2} - N_{k-1/2} + (1/2)(dX_{k+1/2} x F_{k+1/2}
+// + dX_{k-1/2} x F_{k-1/2}) (free ends: missing segments contribute nothing).  Writes the
+// float64 outputs g64/m64 when given, and the float32 copies (X, g, m) the pair sum reads
+// when Xf is given.
+__global__ void rod_node_kernel(const RodLaunch L, const double* __restrict__ X, double* g64,
+                                double* m64, float* Xf, float* gf, float* mf)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.N) return;
+    const int2 ni = L.node_info[k];
+    const double* Xk = X + 3 * (size_t)k;
+    double g[3] = {0, 0, 0}, m[3] = {0, 0, 0};
+    if (ni.x < ni.y - 1) {  // segment k+1/2
+        const double* fn = L.FN + 6 * (size_t)k;
+        const double dX[3] = {Xk[3] - Xk[0], Xk[4] - Xk[1], Xk[5] - Xk[2]};
+        g[0] += fn[0];
+        g[1] += fn[1];
+        g[2] += fn[2];
+        m[0] += fn[3] + 0.5 * (dX[1] * fn[2] - dX[2] * fn[1]);
+        m[1] += fn[4] + 0.5 * (dX[2] * fn[0] - dX[0] * fn[2]);
+        m[2] += fn[5] + 0.5 * (dX[0] * fn[1] - dX[1] * fn[0]);
+    }
+    if (ni.x > 0) {  // segment k-1/2
+        const double* fn = L.FN + 6 * (size_t)(k - 1);
+        const double dX[3] = {Xk[0] - Xk[-3], Xk[1] - Xk[-2], Xk[2] - Xk[-1]};
+        g[0] -= fn[0];
+        g[1] -= fn[1];
+        g[2] -= fn[2];
+        m[0] += -fn[3] + 0.5 * (dX[1] * fn[2] - dX[2] * fn[1]);
+        m[1] += -fn[4] + 0.5 * (dX[2] * fn[0] - dX[0] * fn[2]);
+        m[2] += -fn[5] + 0.5 * (dX[0] * fn[1] - dX[1] * fn[0]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (g64) {
+            g64[3 * (size_t)k + c] = g[c];
+            m64[3 * (size_t)k + c] = m[c];
+        }
+        if (Xf) {
+            Xf[3 * (size_t)k + c] = (float)Xk[c];
+            gf[3 * (size_t)k + c] = (float)g[c];
+            mf[3 * (size_t)k + c] = (float)m[c];
+        }
+    }
+}
+
+// Eq. (newD): rotate the three directors of node k by |w| h about w / |w| (unchanged if w = 0).
+__device__ __forceinline__ void rodrigues(const double* D0, double wx, double wy, double wz,
+                                          double h, double* D1)
+{
+    const double wn = sqrt(wx * wx + wy * wy + wz * wz);
+    if (wn == 0.0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) D1[q] = D0[q];
+        return;
+    }
+    const double e[3] = {wx / wn, wy / wn, wz / wn};
+    double st, ct;
+    sincos(wn * h, &st, &ct);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double* v = D0 + 3 * i;
+        const double ev = e[0] * v[0] + e[1] * v[1] + e[2] * v[2];
+        const double c0 = e[1] * v[2] - e[2] * v[1];
+        const double c1 = e[2] * v[0] - e[0] * v[2];
+        const double c2 = e[0] * v[1] - e[1] * v[0];
+        D1[3 * i + 0] = ct * v[0] + st * c0 + (1.0 - ct) * ev * e[0];
+        D1[3 * i + 1] = ct * v[1] + st * c1 + (1.0 - ct) * ev * e[1];
+        D1[3 * i + 2] = ct * v[2] + st * c2 + (1.0 - ct) * ev * e[2];
+    }
+}
+
+// (X1, D1) = (X0 + u h, Rodrigues(D0, w, h)).  X1/D1 may alias X0/D0.  When bump_step is set,
+// one thread advances the step counter (after every other kernel of the step has read it).
+template <typename VT>
+__global__ void rod_update_kernel(const RodLaunch L, const double* X0, const double* D0,
+                                  const VT* __restrict__ u, const VT* __restrict__ w,
+                                  double h, double* X1, double* D1, int bump_step)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bump_step && k == 0) *L.step += 1;
+    if (k >= L.N) return;
+    double Dn[9], Dl[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Dl[q] = D0[9 * (size_t)k + q];
+    rodrigues(Dl, (double)w[3 * (size_t)k], (double)w[3 * (size_t)k + 1],
+              (double)w[3 * (size_t)k + 2], h, Dn);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) X1[3 * (size_t)k + c] = X0[3 * (size_t)k + c] + (double)u[3 * (size_t)k + c] * h;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) D1[9 * (size_t)k + q] = Dn[q];
+}
+
+static inline int nblk(int n, int b) { return (n + b - 1) / b; }
+
+cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double* D, double t_off,
+                              double* g64, double* m64, float* Xf, float* gf, float* mf,
+                              cudaStream_t s)
+{
+    if (L.N == 0) return cudaSuccess;
+    rod_segment_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, D, t_off);
+    rod_node_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, g64, m64, Xf, gf, mf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rod_update(const RodLaunch& L, const double* X0, const double* D0,
+                              const float* u, const float* w, double h, double* X1, double* D1,
+                              bool bump_step, cudaStream_t s)
+{
+    if (L.N == 0) return cudaSuccess;
+    rod_update_kernel<float><<<nblk(L.N, 128), 128, 0, s>>>(L, X0, D0, u, w, h, X1, D1, bump_step ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rod_update64(const RodLaunch& L, const double* X0, const double* D0,
+                                const double* u, const double* w, double h, double* X1,
+                                double* D1, bool bump_step, cudaStream_t s)
+{
+    if (L.N == 0) return cudaSuccess;
+    rod_update_kernel<double><<<nblk(L.N, 128), 128, 0, s>>>(L, X0, D0, u, w, h, X1, D1, bump_step ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rot_sqrt_batch(int n, const double* R, double* S, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    rot_sqrt_batch_kernel<<<nblk(n, 128), 128, 0, s>>>(n, R, S);
+    return cudaGetLastError();
+}
+
+}  // namespace mrs

@@ -1,0 +1,255 @@
+"""Thin ctypes binding of the C ABI declared in ``include/mrs_gb300.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA library
+``_build/libmrs_gb300.so``.  Device arrays are passed as torch CUDA tensors (their
+``data_ptr()``), host arrays as numpy arrays, streams as ``torch.cuda.Stream`` (or None for
+torch's current stream).  There is no CPU fallback: if the library is missing or a call fails,
+an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmrs_gb300.so")
+
+MRS_OK, MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA, MRS_ETIMEOUT, MRS_ENOCONV, MRS_EBUSY, MRS_PENDING = range(8)
+MRS_F64, MRS_F32, MRS_F32_COMP = 0, 1, 2
+MRS_EULER, MRS_RK2 = 0, 1
+STATUS_NAMES = {0: "MRS_OK", 1: "MRS_EINVAL", 2: "MRS_ENOMEM", 3: "MRS_ECUDA", 4: "MRS_ETIMEOUT",
+                5: "MRS_ENOCONV", 6: "MRS_EBUSY", 7: "MRS_PENDING"}
+
+# Every symbol include/mrs_gb300.h declares (kept in sync by tests/test_abi.py).
+EXPORTS = [
+    "mrs_last_error", "mrs_version", "mrs_ctx_create", "mrs_ctx_destroy", "mrs_ctx_num_sms",
+    "mrs_velocity", "mrs_plan_create", "mrs_plan_execute", "mrs_plan_destroy",
+    "mrs_plan_config_count", "mrs_plan_config_info", "mrs_plan_info",
+    "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run",
+]
+
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class MrsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class RodParams(ctypes.Structure):
+    """``mrs_rod_params``."""
+    _fields_ = [("L", ctypes.c_double), ("a", ctypes.c_double * 3), ("b", ctypes.c_double * 3),
+                ("wave_A", ctypes.c_double), ("wave_k", ctypes.c_double),
+                ("wave_f", ctypes.c_double), ("mu", ctypes.c_double), ("eps", ctypes.c_double)]
+
+    @classmethod
+    def make(cls, L, a, b, wave_A, wave_k, wave_f, mu, eps):
+        p = cls()
+        p.L = L
+        for q in range(3):
+            p.a[q] = a[q]
+            p.b[q] = b[q]
+        p.wave_A, p.wave_k, p.wave_f, p.mu, p.eps = wave_A, wave_k, wave_f, mu, eps
+        return p
+
+
+class PararealStats(ctypes.Structure):
+    """``mrs_parareal_stats``."""
+    _fields_ = [("iterations", ctypes.c_int), ("incr", ctypes.c_double * 64),
+                ("final_incr", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("fine_steps", ctypes.c_int64), ("coarse_steps", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load the library (built by ``paper_2604_12083_gb300.build``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.mrs_last_error.restype = ctypes.c_char_p
+        L.mrs_version.restype = ctypes.c_char_p
+        L.mrs_ctx_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+        L.mrs_ctx_destroy.argtypes = [_vp]
+        L.mrs_ctx_num_sms.argtypes = [_vp]
+        L.mrs_velocity.argtypes = [_vp, ctypes.c_int, _i64p, _vp, _vp, _vp, _vp, _vp, _vp,
+                                   ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _vp]
+        L.mrs_plan_create.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_double, ctypes.c_double,
+                                      _dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
+        L.mrs_plan_execute.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.mrs_plan_destroy.argtypes = [_vp]
+        L.mrs_plan_config_info.argtypes = [_vp, ctypes.c_int, _ip, _ip, _ip]
+        L.mrs_plan_info.argtypes = [_vp, _ip, _i64p, _ip]
+        L.rod_forces.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.POINTER(RodParams), _vp, _vp,
+                                 ctypes.c_double, _vp, _vp, _vp]
+        L.rod_step.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.POINTER(RodParams), _vp, _vp,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, _vp]
+        L.rot_sqrt_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+        L.parareal_run.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.POINTER(RodParams), _vp,
+                                   _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_double, ctypes.POINTER(PararealStats), _vp]
+        _lib = L
+        return L
+
+
+def _check(status):
+    if status != MRS_OK:
+        raise MrsError(status, lib().mrs_last_error().decode())
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (must be contiguous), or None."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to the library must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _offsets(offsets):
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    return off, off.ctypes.data_as(_i64p)
+
+
+class Context:
+    """``mrs_ctx`` on one device."""
+
+    def __init__(self, device: int = 0):
+        self.handle = _vp()
+        _check(lib().mrs_ctx_create(ctypes.byref(self.handle), int(device)))
+        self.device = device
+
+    @property
+    def num_sms(self) -> int:
+        return int(lib().mrs_ctx_num_sms(self.handle))
+
+    def close(self):
+        if self.handle:
+            _check(lib().mrs_ctx_destroy(self.handle))
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mrs_velocity(ctx: Context, offsets, X, f, n, u, w, mu, eps, eps_per_sys=None,
+                 precision=MRS_F32_COMP, Xt=None, stream=None):
+    """``mrs_velocity``: u, w (device tensors, overwritten) from X, f, n (device tensors)."""
+    off, poff = _offsets(offsets)
+    eps_arr = None
+    peps = None
+    if eps_per_sys is not None:
+        eps_arr = np.ascontiguousarray(np.asarray(eps_per_sys, dtype=np.float64))
+        peps = eps_arr.ctypes.data_as(_dp)
+    _check(lib().mrs_velocity(ctx.handle, len(off) - 1, poff, _ptr(X), _ptr(f), _ptr(n), _ptr(Xt),
+                              _ptr(u), _ptr(w), float(mu), float(eps), peps, int(precision),
+                              _stream(stream)))
+
+
+class Plan:
+    """``mrs_plan``: a pair-sum plan built once and executed many times."""
+
+    def __init__(self, ctx: Context, offsets, mu, eps, eps_per_sys=None,
+                 precision=MRS_F32_COMP, config=-1):
+        off, poff = _offsets(offsets)
+        peps = None
+        if eps_per_sys is not None:
+            self._eps = np.ascontiguousarray(np.asarray(eps_per_sys, dtype=np.float64))
+            peps = self._eps.ctypes.data_as(_dp)
+        self.handle = _vp()
+        self.ctx = ctx
+        _check(lib().mrs_plan_create(ctx.handle, len(off) - 1, poff, float(mu), float(eps), peps,
+                                     int(precision), int(config), ctypes.byref(self.handle)))
+
+    def execute(self, X, f, n, u, w, Xt=None, stream=None):
+        _check(lib().mrs_plan_execute(self.handle, _ptr(X), _ptr(f), _ptr(n), _ptr(Xt), _ptr(u),
+                                      _ptr(w), _stream(stream)))
+
+    def info(self):
+        g, c = ctypes.c_int(), ctypes.c_int()
+        wu = ctypes.c_int64()
+        _check(lib().mrs_plan_info(self.handle, ctypes.byref(g), ctypes.byref(wu), ctypes.byref(c)))
+        return {"grid": g.value, "work_units": wu.value, "config": c.value}
+
+    def close(self):
+        if self.handle:
+            _check(lib().mrs_plan_destroy(self.handle))
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_config_count() -> int:
+    return int(lib().mrs_plan_config_count())
+
+
+def plan_config_info(ctx: Context, config: int):
+    t, k, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().mrs_plan_config_info(ctx.handle, int(config), ctypes.byref(t), ctypes.byref(k),
+                                      ctypes.byref(o)))
+    return {"threads": t.value, "targets_per_thread": k.value, "ctas_per_sm": o.value}
+
+
+def rod_forces(ctx: Context, rod_off, params: RodParams, X, D, t, g, m, stream=None):
+    """``rod_forces``: g, m (device float64 tensors, overwritten) from X, D at time t."""
+    off, poff = _offsets(rod_off)
+    _check(lib().rod_forces(ctx.handle, len(off) - 1, poff, ctypes.byref(params), _ptr(X), _ptr(D),
+                            float(t), _ptr(g), _ptr(m), _stream(stream)))
+
+
+def rod_step(ctx: Context, rod_off, params: RodParams, X, D, t0, dt, nsteps, scheme,
+             precision=MRS_F32_COMP, stream=None):
+    """``rod_step``: nsteps steps in place on device float64 tensors X, D."""
+    off, poff = _offsets(rod_off)
+    _check(lib().rod_step(ctx.handle, len(off) - 1, poff, ctypes.byref(params), _ptr(X), _ptr(D),
+                          float(t0), float(dt), int(nsteps), int(scheme), int(precision),
+                          _stream(stream)))
+
+
+def rot_sqrt_batch(ctx: Context, R, S, stream=None):
+    """``rot_sqrt_batch``: S[n,3,3] (device float64, overwritten) = principal sqrt of R[n,3,3]."""
+    _check(lib().rot_sqrt_batch(ctx.handle, int(R.shape[0]), _ptr(R), _ptr(S), _stream(stream)))
+
+
+def parareal_run(ctx: Context, rod_off, params: RodParams, X, D, T0, T1, n_slices, dt_fine,
+                 coarse_ratio, max_iter, tol, stream=None, raise_on_noconv=True):
+    """``parareal_run``: Parareal in place on device float64 X, D; returns the statistics."""
+    off, poff = _offsets(rod_off)
+    st = PararealStats()
+    status = lib().parareal_run(ctx.handle, len(off) - 1, poff, ctypes.byref(params), _ptr(X),
+                                _ptr(D), float(T0), float(T1), int(n_slices), float(dt_fine),
+                                int(coarse_ratio), int(max_iter), float(tol), ctypes.byref(st),
+                                _stream(stream))
+    if status == MRS_ENOCONV and not raise_on_noconv:
+        return st
+    _check(status)
+    return st

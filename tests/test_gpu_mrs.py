@@ -1,0 +1,200 @@
+"""GPU parity of the pair sum (mrs_velocity / plans) against the FP64 CPU oracle.
+
+Bar (per velocity field, over the compared targets): relative L2 error <= 1e-5 for the float32
+paths, <= 1e-12 for the float64 path.  Inputs are float32-representable (see
+paper_2604_12083_gb300.workloads), so both sides see identical positions, forces and torques.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL64 = 1e-12
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_12083_gb300 import build as B, mrs
+    B.build()
+    c = mrs.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def run(ctx, p, precision, config=None, Xt=None):
+    from paper_2604_12083_gb300 import mrs
+    dt = torch.float64 if precision == mrs.MRS_F64 else torch.float32
+    X, f, n = dev(p.X, dt), dev(p.f, dt), dev(p.n, dt)
+    xt = None if Xt is None else dev(Xt, dt)
+    u = torch.full_like(X, float("nan"))
+    w = torch.full_like(X, float("nan"))
+    if config is None:
+        mrs.mrs_velocity(ctx, p.offsets, X, f, n, u, w, p.mu, 0.0, eps_per_sys=p.eps,
+                         precision=precision, Xt=xt)
+    else:
+        pl = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=precision,
+                      config=config)
+        pl.execute(X, f, n, u, w, Xt=xt)
+        torch.cuda.synchronize()
+        pl.close()
+    torch.cuda.synchronize()
+    return u.cpu().numpy().astype(np.float64), w.cpu().numpy().astype(np.float64)
+
+
+def test_plain_rod_float64(ctx, orc):
+    """One rod of 128 nodes, one FP64 call (the plain-method configuration)."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.plain_rod()
+    u, w = run(ctx, p, mrs.MRS_F64)
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+    assert rel_l2(u, ur) < TOL64 and rel_l2(w, wr) < TOL64
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_plain_rod_float32(ctx, orc, precision):
+    from paper_2604_12083_gb300 import workloads as W
+    p = W.plain_rod()
+    u, w = run(ctx, p, precision)
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+    assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
+
+
+def ragged_batch():
+    """Systems of awkward sizes (empty, 1, around the 32-source unit, around 256/512-target
+    tiles, a ragged 4097), placed like the batched workload."""
+    from paper_2604_12083_gb300 import workloads as W
+    rng = np.random.default_rng(60)
+    sizes = [0, 1, 2, 31, 32, 33, 255, 256, 257, 511, 513, 1000, 4097, 0, 3]
+    Xs, fs, ns = [], [], []
+    for s in sizes:
+        X = rng.uniform(0.0, 2.0, (s, 3))
+        Xs.append(X)
+        fs.append(rng.standard_normal((s, 3)))
+        ns.append(rng.standard_normal((s, 3)))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    eps = np.array([float(np.float32(0.01 + 0.002 * i)) for i in range(len(sizes))])
+    f32 = lambda a: np.concatenate(a).astype(np.float32)
+    return W.MRSProblem("ragged", off, f32(Xs), f32(fs), f32(ns), eps, 1.3)
+
+
+@pytest.mark.parametrize("config", list(range(6)))
+@pytest.mark.parametrize("precision", [1, 2])
+def test_ragged_batch_every_config(ctx, orc, config, precision):
+    p = ragged_batch()
+    u, w = run(ctx, p, precision, config=config)
+    ur, wr = orc.mrs_velocity_batch(p.offsets, p.X, p.f, p.n, 0.0, p.mu, eps_per_sys=p.eps)
+    for s in range(len(p.offsets) - 1):
+        a, b = p.offsets[s], p.offsets[s + 1]
+        if a == b:
+            continue
+        assert rel_l2(u[a:b], ur[a:b]) < TOL32, (s, b - a)
+        assert rel_l2(w[a:b], wr[a:b]) < TOL32, (s, b - a)
+
+
+def test_ragged_batch_float64(ctx, orc):
+    from paper_2604_12083_gb300 import mrs
+    p = ragged_batch()
+    u, w = run(ctx, p, mrs.MRS_F64)
+    ur, wr = orc.mrs_velocity_batch(p.offsets, p.X, p.f, p.n, 0.0, p.mu, eps_per_sys=p.eps)
+    for s in range(len(p.offsets) - 1):
+        a, b = p.offsets[s], p.offsets[s + 1]
+        if a < b:
+            assert rel_l2(u[a:b], ur[a:b]) < TOL64 and rel_l2(w[a:b], wr[a:b]) < TOL64
+
+
+def test_separate_targets(ctx, orc):
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.single_system(seed=61, n_fil=3, M=700)
+    rng = np.random.default_rng(61)
+    Xt = (p.X + rng.normal(0, 0.01, p.X.shape)).astype(np.float32)
+    u, w = run(ctx, p, mrs.MRS_F32_COMP, Xt=Xt)
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu, xt=Xt)
+    assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
+
+
+def test_multi_tile_single_system(ctx, orc):
+    """A few thousand points: several tiles, every tile split over many CTAs (fix-up path)."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.single_system(seed=62, n_fil=3, M=1000)      # 3000 points, ragged last tile
+    for prec in (mrs.MRS_F32, mrs.MRS_F32_COMP):
+        u, w = run(ctx, p, prec)
+        ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+        assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
+
+
+def test_deterministic(ctx):
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.single_system(seed=63, n_fil=4, M=1024)
+    a = run(ctx, p, mrs.MRS_F32_COMP)
+    b = run(ctx, p, mrs.MRS_F32_COMP)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_full_size_single_system_sampled(ctx, orc):
+    """32 filaments x 1024 nodes, the benchmark's launch (cached plan, default config): 512
+    sampled targets against all 32768 sources, computed one by one by the oracle."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.single_system()
+    u, w = run(ctx, p, mrs.MRS_F32_COMP)
+    assert np.isfinite(u).all() and np.isfinite(w).all()
+    idx = np.random.default_rng(64).choice(p.n_points, 512, replace=False)
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu, xt=p.X[idx])
+    assert rel_l2(u[idx], ur) < TOL32 and rel_l2(w[idx], wr) < TOL32
+
+
+def test_full_size_batch_sampled(ctx, orc):
+    """512 systems of 256..16384 points in one persistent launch: 4 sampled targets per system
+    against all sources of their own system."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.batch_systems()
+    u, w = run(ctx, p, mrs.MRS_F32)
+    rng = np.random.default_rng(65)
+    eu_n = eu_d = ew_n = ew_d = 0.0
+    for s in range(len(p.offsets) - 1):
+        a, b = int(p.offsets[s]), int(p.offsets[s + 1])
+        idx = rng.choice(b - a, 4, replace=False)
+        ur, wr = orc.mrs_velocity(p.X[a:b], p.f[a:b], p.n[a:b], p.eps[s], p.mu, xt=p.X[a:b][idx])
+        eu_n += np.sum((u[a:b][idx] - ur) ** 2)
+        eu_d += np.sum(ur ** 2)
+        ew_n += np.sum((w[a:b][idx] - wr) ** 2)
+        ew_d += np.sum(wr ** 2)
+    assert np.sqrt(eu_n / eu_d) < TOL32 and np.sqrt(ew_n / ew_d) < TOL32
+
+
+def test_invalid_arguments_rejected(ctx):
+    from paper_2604_12083_gb300 import mrs
+    X = torch.zeros((4, 3), device="cuda")
+    u = torch.zeros_like(X)
+    w = torch.zeros_like(X)
+    with pytest.raises(mrs.MrsError) as e:
+        mrs.mrs_velocity(ctx, [0, 4], X, X, X, u, w, 1.0, -1.0)
+    assert e.value.status == mrs.MRS_EINVAL
+    with pytest.raises(mrs.MrsError):
+        mrs.mrs_velocity(ctx, [0, 3, 2], X, X, X, u, w, 1.0, 0.1)
+    with pytest.raises(mrs.MrsError):
+        mrs.mrs_velocity(ctx, [0, 4], X, X, X, u, u, 1.0, 0.1)   # overlapping outputs
+    with pytest.raises(mrs.MrsError):
+        mrs.mrs_velocity(ctx, [0, 4], X, X, X, u, w, 0.0, 0.1)   # mu = 0
+    # empty problem: a no-op
+    mrs.mrs_velocity(ctx, [0, 0], X, X, X, u, w, 1.0, 0.1)

@@ -1,0 +1,184 @@
+"""GPU parity of the rod path (rotation square root, rod forces, Euler/RK2 steps, Parareal)
+against the FP64 CPU oracle.
+
+Bars: float64 kernels (rotation sqrt, forces) to ~1e-12 relative; time stepping with the
+float32 pair sum <= 1e-4 relative on positions AND on the displacement X(T) - X(0) after the
+stated number of steps; with the float64 pair sum, 1e-9 on the displacement.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table2_rotation_sqrt.json")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_12083_gb300 import build as B, mrs
+    B.build()
+    c = mrs.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def params(W_cfg, eps, mu=1.0):
+    from paper_2604_12083_gb300 import mrs
+    import oracle
+    g = mrs.RodParams.make(W_cfg["L"], W_cfg["a"], W_cfg["b"], W_cfg["wave_A"], W_cfg["wave_k"],
+                           W_cfg["wave_f"], mu, eps)
+    o = oracle.RodParams.make(W_cfg["L"], W_cfg["a"], W_cfg["b"], W_cfg["wave_A"], W_cfg["wave_k"],
+                              W_cfg["wave_f"])
+    return g, o
+
+
+def test_rotation_sqrt_paper_sweep(ctx, orc):
+    """Table 2's sweep (100 angles in [-0.1, pi+0.1], random axes) on the GPU routine."""
+    from scipy.spatial.transform import Rotation
+    from paper_2604_12083_gb300 import mrs
+    g = json.load(open(GOLDEN))
+    rng = np.random.default_rng(70)
+    Rs = []
+    for _ in range(20):
+        ax = rng.standard_normal(3)
+        ax /= np.linalg.norm(ax)
+        for th in np.linspace(-0.1, math.pi + 0.1, 100):
+            Rs.append(Rotation.from_rotvec(ax * th).as_matrix())
+    R = np.array(Rs)
+    Rd = torch.from_numpy(R).cuda()
+    Sd = torch.empty_like(Rd)
+    mrs.rot_sqrt_batch(ctx, Rd, Sd)
+    torch.cuda.synchronize()
+    S = Sd.cpu().numpy()
+    err = np.linalg.norm(S @ S - R, axis=(1, 2))
+    assert err.max() < 1e-13
+    assert err.mean() <= g["cuda_error"]["mean"]
+    orth = np.abs(np.einsum("nij,nkj->nik", S, S) - np.eye(3)).max()
+    assert orth < 1e-14
+    for i in range(0, len(R), 7):
+        np.testing.assert_allclose(S[i], orc.rot_sqrt(R[i]), atol=1e-13)
+
+
+def perturbed(seed, n_rods, M, amp=0.02):
+    from scipy.spatial.transform import Rotation
+    from paper_2604_12083_gb300 import workloads as W
+    rs = W.rod_system(seed, n_rods, M, box=3.0)
+    rng = np.random.default_rng(seed)
+    X = rs.X + amp * rng.standard_normal(rs.X.shape) / M
+    Rr = Rotation.from_rotvec(amp * rng.standard_normal((len(X), 3))).as_matrix()
+    D = np.einsum("krc,kic->kir", Rr, rs.D)
+    return rs, X, D
+
+
+def test_rod_forces_match_oracle(ctx, orc):
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs, X, D = perturbed(71, 1, 17)
+    # three rods of different lengths, including the 2-node minimum
+    rs2, X2, D2 = perturbed(72, 1, 1024)
+    X = np.concatenate([X, np.array([[5.0, 5.0, 5.0], [5.0, 5.0, 5.01]]), X2])
+    D = np.concatenate([D, np.tile(np.eye(3), (2, 1, 1)), D2])
+    off = np.array([0, 17, 19, 19 + 1024], np.int64)
+    gp, op = params(dict(W.ROD_PLAIN), 0.01)
+    for t in (0.0, 0.37):
+        Xd, Dd = torch.from_numpy(X).cuda(), torch.from_numpy(D).cuda()
+        g = torch.empty_like(Xd)
+        m = torch.empty_like(Xd)
+        mrs.rod_forces(ctx, off, gp, Xd, Dd, t, g, m)
+        torch.cuda.synchronize()
+        go, mo = orc.rod_forces(off, X, D, op, t)
+        gg, mm = g.cpu().numpy(), m.cpu().numpy()
+        assert np.abs(gg - go).max() <= 1e-11 * np.abs(go).max()
+        assert np.abs(mm - mo).max() <= 1e-11 * np.abs(mo).max()
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_plain_rod_200_steps(ctx, orc, scheme):
+    """One rod of 128 nodes, 200 steps at dt = 1e-6 (the plain-method configuration)."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(1, 1, 128)
+    cfg = dict(W.ROD_PLAIN)
+    gp, op = params(cfg, rs.eps)
+    Xo, Do = orc.rod_step(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, 0.0, cfg["dt"], 200, scheme)
+    for prec, tol in ((mrs.MRS_F32_COMP, 1e-4), (mrs.MRS_F64, 1e-9)):
+        Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+        mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, 0.0, cfg["dt"], 200, scheme, precision=prec)
+        torch.cuda.synchronize()
+        Xg, Dg = Xd.cpu().numpy(), Dd.cpu().numpy()
+        assert rel(Xg, Xo) < 1e-4
+        assert rel(Xg - rs.X, Xo - rs.X) < tol, (prec, rel(Xg - rs.X, Xo - rs.X))
+        assert rel(Dg - rs.D, Do - rs.D) < 10 * tol
+        assert np.abs(np.einsum("kir,kjr->kij", Dg, Dg) - np.eye(3)).max() < 1e-12
+
+
+def test_multi_rod_rk2_and_resume(ctx, orc):
+    """Four interacting rods; 37 steps in one call equal 20 + 17 steps in two calls."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(73, 4, 64, box=2.0)
+    cfg = dict(W.ROD_PLAIN, a=(2e-3,) * 3, b=(20.0,) * 3)
+    gp, op = params(cfg, rs.eps)
+    dt = 2e-6
+    Xo, _ = orc.rod_step(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, 0.1, dt, 37, orc.RK2)
+    Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+    mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, 0.1, dt, 37, mrs.MRS_RK2)
+    Xa = Xd.cpu().numpy()
+    Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+    mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, 0.1, dt, 20, mrs.MRS_RK2)
+    mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, 0.1 + 20 * dt, dt, 17, mrs.MRS_RK2)
+    Xb = Xd.cpu().numpy()
+    assert rel(Xa - rs.X, Xo - rs.X) < 1e-4
+    assert rel(Xb - rs.X, Xo - rs.X) < 1e-4
+
+
+def test_parareal_matches_oracle_and_serial_fine(ctx, orc):
+    from oracle import parareal as PR
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(74, 2, 24, box=1.5)
+    cfg = dict(W.WAVE, a=(2e-3,) * 3, b=(0.3,) * 3)
+    gp, op = params(cfg, rs.eps)
+    Ns, dt, r = 6, 5e-5, 4
+    T1 = Ns * 16 * dt
+    tol = 1e-10
+    states, incr = PR.rod_parareal(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, 0.0, T1, Ns, dt, r,
+                                   Ns, tol)
+    Xo, _ = PR.unpack_rod_state(states[-1][-1])
+    Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+    st = mrs.parareal_run(ctx, rs.rod_off, gp, Xd, Dd, 0.0, T1, Ns, dt, r, Ns, tol)
+    Xg = Xd.cpu().numpy()
+    assert rel(Xg - rs.X, Xo - rs.X) < 1e-4
+    assert abs(st.iterations - len(incr)) <= 1
+    # the first increments follow the oracle's (before either reaches float32 round-off)
+    assert abs(st.incr[0] - incr[0]) <= 1e-3 * incr[0]
+    # converged Parareal equals serial fine stepping
+    Xs, Ds = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+    mrs.rod_step(ctx, rs.rod_off, gp, Xs, Ds, 0.0, dt, Ns * 16, mrs.MRS_RK2)
+    assert rel(Xg - rs.X, Xs.cpu().numpy() - rs.X) < 1e-5
+    assert st.fine_steps > 0 and st.coarse_steps > 0
+
+
+def test_rod_invalid_arguments(ctx):
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    X = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+    D = torch.zeros((4, 3, 3), dtype=torch.float64, device="cuda")
+    gp, _ = params(dict(W.ROD_PLAIN), 0.01)
+    with pytest.raises(mrs.MrsError):
+        mrs.rod_step(ctx, [0, 1, 4], gp, X, D, 0.0, 1e-6, 1, 0)      # 1-node rod
+    with pytest.raises(mrs.MrsError):
+        mrs.rod_step(ctx, [0, 4], gp, X, D, 0.0, -1.0, 1, 0)          # dt < 0
+    with pytest.raises(mrs.MrsError):
+        mrs.parareal_run(ctx, [0, 4], gp, X, D, 0.0, 1e-3, 3, 1e-4, 4, 3, 1e-9)  # ragged slices
