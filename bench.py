@@ -42,6 +42,20 @@ def load_peaks():
         return {}
 
 
+def measured_traffic():
+    """DRAM bytes per launch of the pair-sum kernel from the committed ncu capture, or None when
+    the kernel source has changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "mrs_traffic.json")))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+    except Exception:
+        return None
+
+
 def fp32_peak_tflops(n_sms, peaks):
     """2 flops (FMA) x 128 FP32 lanes per SM x SMs x the maximum SM clock."""
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -434,7 +448,7 @@ def run_ours(args, world, rank, local, pg):
                    "l2": "flushed before every timed step (512 MiB write)"},
         "rel_err": rel,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": measured_traffic(),
                      "peak_basis": "2 x 128 FP32 lanes x %d SMs x %.0f MHz (max SM clock)" %
                                    (ctx.num_sms, mhz),
                      "flops_per_pair": FLOPS_PER_PAIR, "kernel": "mrs_f32_persistent"},
