@@ -116,6 +116,27 @@ MRS_API int mrs_velocity(mrs_ctx* ctx, int n_sys, const int64_t* offsets,
                  void* u, void* w, double mu, double eps, const double* eps_per_sys,
                  int precision, void* stream);
 
+/* Pair sum that allocates nothing (the paper has no counterpart: this is a library service).
+ * For callers that cannot call cudaMalloc -- code whose device memory belongs to another
+ * allocator or a fixed budget, latency-critical loops that cannot pay for cudaMalloc's implicit
+ * device synchronisation, or code running while another component captures the stream.
+ * Computes the same sum as mrs_velocity for ONE system (targets = sources), float32 with
+ * compensated accumulation (MRS_F32_COMP), on the calling thread's current device:
+ *   n_points     number of points, 0 <= n_points <= 1048576 (larger: MRS_EINVAL with a message)
+ *   X, f, n      device float32 [n_points][3] positions, forces, torques (caller-owned)
+ *   u, w         device float32 [n_points][3] outputs (caller-owned, overwritten)
+ *   mu, eps      viscosity (> 0) and regularisation (> 0)
+ * Scratch (work table, partial results, tile counters) lives in a fixed ~18.3 MiB __device__
+ * array that every GPU loading the library holds until the process exits.  The FIRST call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and the device's SM count;
+ * make that first call before any stream capture.  No call allocates or frees memory.  Every
+ * call shares the one array and each call re-initialises what must start at zero, so calls
+ * whose GPU work overlaps (other streams, other host threads) race and give wrong results:
+ * issue them on one stream.
+ * Errors: MRS_EINVAL, MRS_ECUDA. */
+MRS_API int mrs_velocity_noalloc(int64_t n_points, const float* X, const float* f, const float* n,
+                                 float* u, float* w, double mu, double eps, void* stream);
+
 /* Explicit plans: build once, then execute many times (e.g. inside a CUDA graph).
  *   config  -1: the library's choice (tuned table or heuristic); otherwise an index into
  *           mrs_plan_config_count() kernel configurations (tile shape / targets per thread).

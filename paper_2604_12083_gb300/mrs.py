@@ -28,7 +28,7 @@ EXPORTS = [
     "mrs_last_error", "mrs_version", "mrs_ctx_create", "mrs_ctx_destroy", "mrs_ctx_num_sms",
     "mrs_velocity", "mrs_plan_create", "mrs_plan_execute", "mrs_plan_destroy",
     "mrs_plan_config_count", "mrs_plan_config_info", "mrs_plan_info",
-    "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run",
+    "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run", "mrs_velocity_noalloc",
 ]
 
 _vp = ctypes.c_void_p
@@ -100,6 +100,8 @@ def lib():
                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, _vp]
         L.rot_sqrt_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+        L.mrs_velocity_noalloc.argtypes = [ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
+                                           ctypes.c_double, ctypes.c_double, _vp]
         L.parareal_run.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.POINTER(RodParams), _vp,
                                    _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -169,6 +171,13 @@ def mrs_velocity(ctx: Context, offsets, X, f, n, u, w, mu, eps, eps_per_sys=None
     _check(lib().mrs_velocity(ctx.handle, len(off) - 1, poff, _ptr(X), _ptr(f), _ptr(n), _ptr(Xt),
                               _ptr(u), _ptr(w), float(mu), float(eps), peps, int(precision),
                               _stream(stream)))
+
+
+def mrs_velocity_noalloc(n_points, X, f, n, u, w, mu, eps, stream=None):
+    """``mrs_velocity_noalloc``: one system, float32 compensated, no device allocation (for
+    callers that must not allocate); u, w (device float32 tensors) are overwritten."""
+    _check(lib().mrs_velocity_noalloc(int(n_points), _ptr(X), _ptr(f), _ptr(n), _ptr(u), _ptr(w),
+                                      float(mu), float(eps), _stream(stream)))
 
 
 class Plan:
