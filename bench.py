@@ -229,6 +229,8 @@ def extra_batch(ctx, dev):
     u = torch.empty_like(X)
     w = torch.empty_like(X)
     stream = torch.cuda.current_stream(dev)
+    tuned_cfg, tuned_ms = mrs.autotune(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps,
+                                       precision=mrs.MRS_F32, reps=2)
     plan = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32)
     plan.execute(X, f, n, u, w)
     torch.cuda.synchronize()
@@ -274,7 +276,8 @@ def extra_batch(ctx, dev):
             "persistent_pairs_per_s": p.pairs / (ms_graph * 1e-3),
             "one_launch_per_system_ms": ms_loop,
             "one_launch_per_system_pairs_per_s": p.pairs / (ms_loop * 1e-3),
-            "speedup": ms_loop / ms_graph, "rel_err_sampled": rel_batch, "plan": info}
+            "speedup": ms_loop / ms_graph, "rel_err_sampled": rel_batch, "plan": info,
+            "autotuned_config": tuned_cfg, "autotune_best_ms": tuned_ms}
 
 
 def extra_rod_step(ctx, dev):
@@ -330,10 +333,98 @@ def extra_parareal(ctx, dev):
             "rel_diff_vs_serial_displacement": float(np.linalg.norm(disp_p - disp_s) / np.linalg.norm(disp_s))}
 
 
+def _serve_jobs(trace, dev, seed):
+    """Device buffers for every job of a trace (built before any timing)."""
+    import torch
+    from paper_2604_12083_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for (t, kind, N) in trace:
+        n_fil = N // 256
+        X, D = W.place_filaments(rng, n_fil, 256, box=10.0)
+        eps = float(np.float32(W.EPS_OVER_DS / 255))
+        if kind == 0:
+            f = rng.standard_normal((N, 3)).astype(np.float32)
+            n = rng.standard_normal((N, 3)).astype(np.float32)
+            b = [torch.from_numpy(a.astype(np.float32)).to(dev) for a in (X, f, n)]
+            b += [torch.empty_like(b[0]), torch.empty_like(b[0])]
+        else:
+            b = [torch.from_numpy(X).to(dev), torch.from_numpy(D).to(dev),
+                 np.arange(0, N + 1, 256, dtype=np.int64)]
+        jobs.append((t, kind, N, eps, b))
+    return jobs
+
+
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def extra_serve(ctx, dev):
+    """Poisson arrivals of mixed jobs (70 % one pair sum, 30 % 100-step Euler rod integration),
+    N log-uniform in [1k, 64k] (filaments of 256 nodes): the continuous-batching server vs the
+    same jobs run one request per launch, both on this GPU."""
+    import torch
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    c = W.ROD_PLAIN
+    out = {"workload": "Poisson arrivals, 70% mrs_velocity / 30% 100-step Euler rod jobs, "
+                       "N log-uniform [1k,64k], HBM budget 150 GB"}
+    for label, rate, window, seed in (("nominal_2000_per_s", 2000.0, 0.05, 5),
+                                      ("rate_20_per_s", 20.0, 2.0, 6), ("rate_5_per_s", 5.0, 2.0, 7)):
+        trace = W.serve_trace(seed=seed, rate_hz=rate, window_s=window)
+        jobs = _serve_jobs(trace, dev, seed)
+        pairs = sum((N * N) * (1 if k == 0 else 100) for (_, k, N, _, _) in jobs)
+        res = {"jobs": len(jobs), "pairs": float(pairs)}
+        for mode in ("served", "one_request_per_launch"):
+            torch.cuda.synchronize()
+            lat = []
+            if mode == "served":
+                srv = mrs.Server(ctx, 150 * 10**9, 256)
+                tickets = []
+                t0 = time.perf_counter()
+                for (ta, kind, N, eps, b) in jobs:
+                    while time.perf_counter() - t0 < ta:
+                        time.sleep(2e-4)
+                    if kind == 0:
+                        tickets.append(srv.submit_velocity(b[0], b[1], b[2], b[3], b[4], 1.0, eps))
+                    else:
+                        prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"],
+                                                 c["wave_f"], 1.0, eps)
+                        tickets.append(srv.submit_rod(b[2], b[0], b[1], prm, 0.0, c["dt"], 100,
+                                                      mrs.MRS_EULER, 1.0, eps))
+                srv.drain(900.0)
+                makespan = time.perf_counter() - t0
+                lat = [srv.poll(t)[1] for t in tickets]
+                res["served_stats"] = srv.stats()
+                srv.close()
+            else:
+                s = torch.cuda.current_stream(dev)
+                t0 = time.perf_counter()
+                for (ta, kind, N, eps, b) in jobs:
+                    while time.perf_counter() - t0 < ta:
+                        time.sleep(2e-4)
+                    if kind == 0:
+                        mrs.mrs_velocity(ctx, [0, N], b[0], b[1], b[2], b[3], b[4], 1.0, eps)
+                    else:
+                        prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"],
+                                                 c["wave_f"], 1.0, eps)
+                        mrs.rod_step(ctx, b[2], prm, b[0], b[1], 0.0, c["dt"], 100, mrs.MRS_EULER)
+                    s.synchronize()
+                    lat.append(time.perf_counter() - t0 - ta)
+                makespan = time.perf_counter() - t0
+            res[mode] = {"makespan_s": makespan, "pairs_per_s": pairs / makespan,
+                         "p50_latency_s": _pct(lat, 50), "p99_latency_s": _pct(lat, 99)}
+        res["throughput_ratio_served_vs_plain"] = (res["served"]["pairs_per_s"] /
+                                                   res["one_request_per_launch"]["pairs_per_s"])
+        out[label] = res
+        del jobs
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_extras(ctx, dev):
     out = {}
     for name, fn in (("batch", extra_batch), ("rod_step", extra_rod_step),
-                     ("parareal", extra_parareal)):
+                     ("parareal", extra_parareal), ("serve", extra_serve)):
         try:
             out[name] = fn(ctx, dev)
         except Exception as e:       # reported, never silently replaced by another path

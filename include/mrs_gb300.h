@@ -149,6 +149,19 @@ MRS_API int mrs_plan_execute(mrs_plan* plan, const void* X, const void* f, const
                      const void* Xt, void* u, void* w, void* stream);
 MRS_API int mrs_plan_destroy(mrs_plan* plan);
 
+/* Autotuner: time every kernel configuration on this batch shape (synthetic inputs generated
+ * on the device; temporary buffers allocated and freed here), `reps` timed runs each, and
+ * remember the fastest for the shape's bucket (precision, log2 of #systems, of total points and
+ * of the largest system) in the context; plans created with config = -1 then use it.
+ * Float32 precisions only.  Synchronizes the device.  Outputs (host) may be NULL.
+ * Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */
+MRS_API int mrs_autotune(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
+                         const double* eps_per_sys, int precision, int reps, int* best_config,
+                         float* best_ms);
+/* Write / read the context's tuning table as JSON (tied to the device architecture). */
+MRS_API int mrs_autotune_save(const mrs_ctx* ctx, const char* path);
+MRS_API int mrs_autotune_load(mrs_ctx* ctx, const char* path);
+
 /* Kernel configurations available to plans: count, and a description of entry `config`
  * (threads per CTA, targets per thread, CTAs resident per SM on this device). */
 MRS_API int mrs_plan_config_count(void);
@@ -228,6 +241,71 @@ MRS_API int parareal_run(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const
                  double* X, double* D, double T0, double T1, int n_slices, double dt_fine,
                  int coarse_ratio, int max_iter, double tol, mrs_parareal_stats* out,
                  void* stream);
+
+/* ==========================================================================================
+ * Serving -- continuous batching of pair-sum and rod-integration jobs on one GPU.
+ * (The paper has no serving layer; this is the library's request loop around the method.)
+ *
+ * A server owns one CUDA stream, a device memory pool of hbm_budget_bytes and a scheduler
+ * thread.  Jobs are admitted, in submission order, as soon as a slot (max_slots) and pool
+ * memory for their footprint are free.  Every scheduler iteration advances ALL admitted jobs
+ * by one stage -- a velocity job is one stage, a rod job one stage per Euler step (two per
+ * RK2 step) -- and the pair sums of all of them run as ONE persistent kernel launch, so jobs
+ * that arrive while others are on the GPU join the next iteration and their work overlaps.
+ * Inputs are copied into the pool when the job is admitted and results are copied out when
+ * it finishes; the caller's buffers must stay valid and unmodified until serve_poll reports
+ * the job done.
+ * ========================================================================================== */
+typedef struct mrs_server mrs_server;
+
+#define MRS_JOB_VELOCITY 0   /* one mrs_velocity (float32, compensated) of one system */
+#define MRS_JOB_ROD      1   /* nsteps rod_step steps of one system of rods */
+
+typedef struct {
+    int kind;                 /* MRS_JOB_VELOCITY | MRS_JOB_ROD */
+    int64_t n_points;         /* points (velocity job) or nodes of all rods (rod job), >= 1 */
+    double mu, eps;           /* viscosity and regularisation of the job's system (> 0) */
+    /* velocity job: device float32 [n_points][3] inputs and outputs */
+    const float* X;
+    const float* f;
+    const float* n;
+    float* u;
+    float* w;
+    /* rod job: host rod offsets (n_rods+1, copied at submit), device float64 state advanced in
+     * place (X [n_points][3], D [n_points][3][3]); params.mu/eps are ignored (mu, eps above) */
+    int n_rods;
+    const int64_t* rod_off;
+    double* Xr;
+    double* Dr;
+    mrs_rod_params params;
+    double t0, dt;
+    int nsteps;
+    int scheme;               /* MRS_EULER | MRS_RK2 */
+} mrs_job;
+
+/* Create a server on the context's device: pool of hbm_budget_bytes (allocated here, once),
+ * at most max_slots jobs admitted at a time.  Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */
+MRS_API int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int max_slots);
+
+/* Queue a job (host call, never blocks on the GPU).  *ticket identifies it for serve_poll.
+ * Errors: MRS_EINVAL (bad sizes/pointers), MRS_EBUSY (the job alone exceeds the pool). */
+MRS_API int serve_submit(mrs_server* srv, const mrs_job* job, uint64_t* ticket);
+
+/* Non-blocking status: *done = 1 and *latency_s = completion time - submit time once the job
+ * has finished and its results are in the caller's buffers; returns MRS_PENDING (done = 0)
+ * while it is queued or running, MRS_OK when done, or the job's error status. */
+MRS_API int serve_poll(mrs_server* srv, uint64_t ticket, int* done, double* latency_s);
+
+/* Block until every submitted job has finished (or timeout_s seconds pass: MRS_ETIMEOUT). */
+MRS_API int serve_drain(mrs_server* srv, double timeout_s);
+
+/* Counters: iterations run, jobs completed, pair interactions computed, peak jobs admitted at
+ * once, peak pool bytes in use. */
+MRS_API int serve_stats(mrs_server* srv, int64_t* iterations, int64_t* completed, double* pairs,
+                        int* peak_active, size_t* peak_pool_bytes);
+
+/* Stop the scheduler (after the queued work finishes) and free the pool. */
+MRS_API int serve_destroy(mrs_server* srv);
 
 #ifdef __cplusplus
 }

@@ -69,6 +69,7 @@ struct SysConst {  // per-system constants of the scaled kernels (see mrs_kernel
 struct KernelConfig {
     int threads;   // threads per CTA
     int tpt;       // targets per thread
+    int paired;    // 1: packed f32x2 inner loop (two sources per instruction)
 };
 
 // Configurations compiled into the library (index = plan config id).
@@ -111,6 +112,23 @@ struct MrsLaunch64 {
 };
 cudaError_t launch_mrs_f64(const MrsLaunch64& L, cudaStream_t s);
 constexpr int kF64Block = 128;
+
+// Autotuning: best configuration per batch-shape bucket (precision, log2 of the number of
+// systems, of the total points and of the largest system).
+struct TuneKey {
+    int precision, sys_log2, n_log2, max_log2;
+    bool operator==(const TuneKey& o) const
+    {
+        return precision == o.precision && sys_log2 == o.sys_log2 && n_log2 == o.n_log2 &&
+               max_log2 == o.max_log2;
+    }
+};
+struct TuneEntry {
+    TuneKey key;
+    int config;
+    float ms;
+};
+TuneKey tune_key(int n_sys, const int64_t* offsets, int precision);
 
 struct RodWorkspace;
 void rod_ws_free(RodWorkspace* ws);
@@ -158,6 +176,8 @@ struct mrs_ctx {
     // rod workspaces used by rod_forces / rod_step / parareal_run (LRU, most recent first)
     std::list<mrs::RodWorkspace*> rod_ws;
     size_t rod_ws_max = 96;
+    // measured best kernel configurations (mrs_autotune)
+    std::vector<mrs::TuneEntry> tuned;
 };
 
 namespace mrs {
@@ -167,4 +187,5 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
              void* w, cudaStream_t s);
 void plan_free(mrs_plan* p);
 int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precision);
+int tuned_config(const mrs_ctx* ctx, const TuneKey& k);
 }  // namespace mrs

@@ -26,7 +26,7 @@
 //     into a per-target Kahan pair (sum, compensation) held in shared memory.
 //   * A tile whose units are spread over several CTAs: each CTA writes its partial to its own
 //     scratch slot, then adds its unit count to the tile's counter; the CTA that completes the
-//     count sums all slots in CTA order (float64) and writes the result, then zeroes the
+//     count sums all slots in CTA order (float32 Kahan) and writes the result, then zeroes the
 //     counter for the next launch.  No CTA ever waits for another.
 //
 // Float64 path (MRS_F64): one CTA per 128 targets, all sources of the system staged through
@@ -100,6 +100,74 @@ __device__ __forceinline__ void pair_f32(float xi, float yi, float zi, const flo
     acc[5] = fmaf(-hfy, rx, acc[5]);
 }
 
+// Packed form of pair_f32: the two lanes of every float2 hold two different sources (j, j+1)
+// for the same target, so each f32x2 instruction does the work of two scalar ones.  q = X - x
+// (the negated separation; every term below is written in q: (f.r) r = (f.q) q and
+// n x r = q x n), so the staged positions need no negation.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void pair_f32x2(const float2 xt, const float2 yt, const float2 zt,  // targets
+                                           const float2 X0, const float2 X1, const float2 X2,
+                                           const float2 F0, const float2 F1, const float2 F2,
+                                           const float2 N0, const float2 N1, const float2 N2,
+                                           const float2 e2, const float2 c1, const float2 c2,
+                                           const float2 c3, const float2 c5, float2* acc)
+{
+    const float2 qx = __fadd2_rn(X0, neg2(xt)), qy = __fadd2_rn(X1, neg2(yt)),
+                 qz = __fadd2_rn(X2, neg2(zt));
+    const float2 d = __ffma2_rn(qx, qx, __ffma2_rn(qy, qy, __ffma2_rn(qz, qz, e2)));
+    const float2 s = make_float2(sfu_rsqrt(d.x), sfu_rsqrt(d.y));
+    const float2 s2 = make_float2(sfu_rcp(d.x), sfu_rcp(d.y));
+    const float2 s3 = __fmul2_rn(s, s2);
+    const float2 s5 = __fmul2_rn(s3, s2);
+    const float2 h1 = __ffma2_rn(e2, s3, s);
+    const float2 h3 = __ffma2_rn(c1, s5, s3);
+    const float2 h4 = __fmul2_rn(s3, __ffma2_rn(s2, __ffma2_rn(c2, s2, c3), f2(-0.5f)));
+    const float2 h5 = __fmul2_rn(s5, __ffma2_rn(c5, s2, f2(1.5f)));
+    const float2 fq = __ffma2_rn(F0, qx, __ffma2_rn(F1, qy, __fmul2_rn(F2, qz)));
+    const float2 nq = __ffma2_rn(N0, qx, __ffma2_rn(N1, qy, __fmul2_rn(N2, qz)));
+    const float2 bf = __fmul2_rn(s3, fq);
+    const float2 bn = __fmul2_rn(h5, nq);
+    const float2 hn0 = __fmul2_rn(h3, N0), hn1 = __fmul2_rn(h3, N1), hn2 = __fmul2_rn(h3, N2);
+    // u += H1 f + H2 (f.q) q + H3 (q x n)
+    acc[0] = __ffma2_rn(h1, F0, acc[0]);
+    acc[1] = __ffma2_rn(h1, F1, acc[1]);
+    acc[2] = __ffma2_rn(h1, F2, acc[2]);
+    acc[0] = __ffma2_rn(bf, qx, acc[0]);
+    acc[1] = __ffma2_rn(bf, qy, acc[1]);
+    acc[2] = __ffma2_rn(bf, qz, acc[2]);
+    acc[0] = __ffma2_rn(qy, hn2, acc[0]);
+    acc[1] = __ffma2_rn(qz, hn0, acc[1]);
+    acc[2] = __ffma2_rn(qx, hn1, acc[2]);
+    acc[0] = __ffma2_rn(neg2(qz), hn1, acc[0]);
+    acc[1] = __ffma2_rn(neg2(qx), hn2, acc[1]);
+    acc[2] = __ffma2_rn(neg2(qy), hn0, acc[2]);
+    // omega += H3 (q x f) + H4 n + H5 (n.q) q
+    const float2 hf0 = __fmul2_rn(h3, F0), hf1 = __fmul2_rn(h3, F1), hf2 = __fmul2_rn(h3, F2);
+    acc[3] = __ffma2_rn(h4, N0, acc[3]);
+    acc[4] = __ffma2_rn(h4, N1, acc[4]);
+    acc[5] = __ffma2_rn(h4, N2, acc[5]);
+    acc[3] = __ffma2_rn(bn, qx, acc[3]);
+    acc[4] = __ffma2_rn(bn, qy, acc[4]);
+    acc[5] = __ffma2_rn(bn, qz, acc[5]);
+    acc[3] = __ffma2_rn(qy, hf2, acc[3]);
+    acc[4] = __ffma2_rn(qz, hf0, acc[4]);
+    acc[5] = __ffma2_rn(qx, hf1, acc[5]);
+    acc[3] = __ffma2_rn(neg2(qz), hf1, acc[3]);
+    acc[4] = __ffma2_rn(neg2(qx), hf2, acc[4]);
+    acc[5] = __ffma2_rn(neg2(qy), hf0, acc[5]);
+}
+
+// Kahan step: (sum, comp) += v, with sum - comp the compensated total.
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float v)
+{
+    const float y = __fsub_rn(v, comp);
+    const float t = __fadd_rn(sum, y);
+    comp = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
 __device__ __forceinline__ long long unit_start(long long W, int P, int p)
 {
     return (W * (long long)p) / (long long)P;
@@ -115,13 +183,16 @@ __device__ __forceinline__ int cta_of_unit(long long W, int P, long long x)
     return q;
 }
 
-template <int BLOCK>
+template <int BLOCK, int TPT>
 struct MinBlocks {
-    static constexpr int value = BLOCK >= 256 ? 2 : (BLOCK >= 128 ? 4 : 8);
+    static constexpr int value = BLOCK >= 256 ? 2 : (BLOCK >= 128 ? (TPT >= 8 ? 3 : 4) : 8);
 };
 
-template <int BLOCK, int TPT, bool COMP>
-__global__ void __launch_bounds__(BLOCK, MinBlocks<BLOCK>::value)
+// PAIRED: the inner loop runs on packed f32x2 instructions, two sources per instruction
+// (pair_f32x2); sources are then staged structure-of-arrays (nine rows of kChunk floats) so
+// that four consecutive sources of one component are one 16-byte shared load.
+template <int BLOCK, int TPT, bool COMP, bool PAIRED>
+__global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, TPT>::value))
 mrs_f32_persistent(const MrsLaunch L)
 {
     constexpr int TM = BLOCK * TPT;
@@ -135,11 +206,13 @@ mrs_f32_persistent(const MrsLaunch L)
     const long long uend = unit_start(L.W, L.P, p + 1);
     if (ubeg >= uend) return;
 
-    // lanes 9..11 of every staged source stay zero
-    for (int i = tid; i < kChunk; i += BLOCK) {
-        sflat[i * 12 + 9] = 0.f;
-        sflat[i * 12 + 10] = 0.f;
-        sflat[i * 12 + 11] = 0.f;
+    if (!PAIRED) {
+        // lanes 9..11 of every staged source stay zero
+        for (int i = tid; i < kChunk; i += BLOCK) {
+            sflat[i * 12 + 9] = 0.f;
+            sflat[i * 12 + 10] = 0.f;
+            sflat[i * 12 + 11] = 0.f;
+        }
     }
     // first tile: the last one whose first unit is <= ubeg
     int ti;
@@ -162,6 +235,7 @@ mrs_f32_persistent(const MrsLaunch L)
 
         float xt[TPT][3];
         float acc[TPT][6];
+        float2 acc2[TPT][6];
 #pragma unroll
         for (int k = 0; k < TPT; ++k) {
             const int li = k * BLOCK + tid;
@@ -169,7 +243,10 @@ mrs_f32_persistent(const MrsLaunch L)
 #pragma unroll
             for (int c = 0; c < 3; ++c) xt[k][c] = L.Xt[gi * 3 + c];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) acc[k][q] = 0.f;
+            for (int q = 0; q < 6; ++q) {
+                acc[k][q] = 0.f;
+                acc2[k][q] = make_float2(0.f, 0.f);
+            }
             if (COMP) {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) kah[(q * TPT + k) * BLOCK + tid] = make_float2(0.f, 0.f);
@@ -187,25 +264,70 @@ mrs_f32_persistent(const MrsLaunch L)
             const float* gn = L.n + j0 * 3;
             for (int idx = tid; idx < cnt * 3; idx += BLOCK) {
                 const int sidx = idx / 3, c = idx - sidx * 3;
-                sflat[sidx * 12 + c] = __ldg(gX + idx);
-                sflat[sidx * 12 + 3 + c] = __ldg(gf + idx);
-                sflat[sidx * 12 + 6 + c] = __ldg(gn + idx);
+                if (PAIRED) {
+                    sflat[c * kChunk + sidx] = __ldg(gX + idx);
+                    sflat[(3 + c) * kChunk + sidx] = __ldg(gf + idx);
+                    sflat[(6 + c) * kChunk + sidx] = __ldg(gn + idx);
+                } else {
+                    sflat[sidx * 12 + c] = __ldg(gX + idx);
+                    sflat[sidx * 12 + 3 + c] = __ldg(gf + idx);
+                    sflat[sidx * 12 + 6 + c] = __ldg(gn + idx);
+                }
             }
             for (int sidx = cnt + tid; sidx < cntp; sidx += BLOCK) {
 #pragma unroll
-                for (int c = 0; c < 9; ++c) sflat[sidx * 12 + c] = 0.f;  // zero source: adds 0
+                for (int c = 0; c < 9; ++c) {
+                    if (PAIRED) sflat[c * kChunk + sidx] = 0.f;   // zero source: adds 0
+                    else sflat[sidx * 12 + c] = 0.f;
+                }
             }
             __syncthreads();
 
-            const float e2 = sc.e2, c1 = sc.c1, c2 = sc.c2, c3 = sc.c3, c5 = sc.c5;
-#pragma unroll 2
-            for (int j = 0; j < cntp; ++j) {
-                const float4 a = *reinterpret_cast<const float4*>(&sflat[j * 12]);
-                const float4 b = *reinterpret_cast<const float4*>(&sflat[j * 12 + 4]);
-                const float nz = sflat[j * 12 + 8];
+            if (PAIRED) {
+                const float2 e2 = f2(sc.e2), c1 = f2(sc.c1), c2 = f2(sc.c2), c3 = f2(sc.c3),
+                             c5 = f2(sc.c5);
+                float2 xn[TPT][3];
 #pragma unroll
                 for (int k = 0; k < TPT; ++k)
-                    pair_f32(xt[k][0], xt[k][1], xt[k][2], a, b, nz, e2, c1, c2, c3, c5, acc[k]);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) xn[k][c] = f2(xt[k][c]);
+#pragma unroll 1
+                for (int j = 0; j < cntp; j += 4) {
+                    float4 v[9];
+#pragma unroll
+                    for (int c = 0; c < 9; ++c)
+                        v[c] = *reinterpret_cast<const float4*>(&sflat[c * kChunk + j]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float2 s9[9];
+#pragma unroll
+                        for (int c = 0; c < 9; ++c)
+                            s9[c] = h == 0 ? make_float2(v[c].x, v[c].y) : make_float2(v[c].z, v[c].w);
+#pragma unroll
+                        for (int k = 0; k < TPT; ++k)
+                            pair_f32x2(xn[k][0], xn[k][1], xn[k][2], s9[0], s9[1], s9[2], s9[3],
+                                       s9[4], s9[5], s9[6], s9[7], s9[8], e2, c1, c2, c3, c5,
+                                       acc2[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < TPT; ++k)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        acc[k][q] = __fadd_rn(acc[k][q], __fadd_rn(acc2[k][q].x, acc2[k][q].y));
+                        acc2[k][q] = make_float2(0.f, 0.f);
+                    }
+            } else {
+                const float e2 = sc.e2, c1 = sc.c1, c2 = sc.c2, c3 = sc.c3, c5 = sc.c5;
+#pragma unroll 2
+                for (int j = 0; j < cntp; ++j) {
+                    const float4 a = *reinterpret_cast<const float4*>(&sflat[j * 12]);
+                    const float4 b = *reinterpret_cast<const float4*>(&sflat[j * 12 + 4]);
+                    const float nz = sflat[j * 12 + 8];
+#pragma unroll
+                    for (int k = 0; k < TPT; ++k)
+                        pair_f32(xt[k][0], xt[k][1], xt[k][2], a, b, nz, e2, c1, c2, c3, c5, acc[k]);
+                }
             }
             if (COMP) {
                 // Kahan fold of this chunk's partial into (sum, compensation)
@@ -237,7 +359,7 @@ mrs_f32_persistent(const MrsLaunch L)
                         float v;
                         if (COMP) {
                             const float2 sc2 = kah[(q * TPT + k) * BLOCK + tid];
-                            v = (float)((double)sc2.x - (double)sc2.y);
+                            v = __fsub_rn(sc2.x, sc2.y);
                         } else {
                             v = acc[k][q];
                         }
@@ -273,38 +395,49 @@ mrs_f32_persistent(const MrsLaunch L)
             __syncthreads();
             if (s_last) {
                 __threadfence();
+                // float32 Kahan sum over the slots, in CTA order (float64 is a slow pipe here).
+                // Contributors are the consecutive CTAs q_lo..q_hi (every CTA range is non-empty
+                // because P <= W).  Only q_lo can have started before this tile, in which case
+                // the tile is its second segment (slot 2 q_lo + 1); for every later CTA it is the
+                // first segment (slot 2 qc).  Slots are read four at a time to keep loads in
+                // flight; the sum order stays the CTA order.
                 const int q_lo = cta_of_unit(L.W, L.P, T.u0);
                 const int q_hi = cta_of_unit(L.W, L.P, T.u0 + T.nu - 1);
-                double tot[TPT][6];
-#pragma unroll
-                for (int k = 0; k < TPT; ++k)
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) tot[k][q] = 0.0;
-                for (int qc = q_lo; qc <= q_hi; ++qc) {
-                    const long long st = unit_start(L.W, L.P, qc);
-                    if (st == unit_start(L.W, L.P, qc + 1)) continue;   // empty CTA range
-                    const int sl = 2 * qc + (st < T.u0 ? 1 : 0);
-                    const float* pp = L.partial + (size_t)sl * 12 * TM;
-#pragma unroll
-                    for (int k = 0; k < TPT; ++k) {
-                        const int li = k * BLOCK + tid;
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) {
-                            double v = (double)__ldcg(pp + q * TM + li);
-                            if (COMP) v -= (double)__ldcg(pp + (6 + q) * TM + li);
-                            tot[k][q] += v;
-                        }
-                    }
-                }
-#pragma unroll
+                const int sl_lo = 2 * q_lo + (unit_start(L.W, L.P, q_lo) < T.u0 ? 1 : 0);
+                constexpr int NV = COMP ? 12 : 6;
+#pragma unroll 1
                 for (int k = 0; k < TPT; ++k) {
                     const int li = k * BLOCK + tid;
+                    float tot[6], cmp[6];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        tot[q] = 0.f;
+                        cmp[q] = 0.f;
+                    }
+                    for (int qb = q_lo; qb <= q_hi; qb += 4) {
+                        float v[4][NV];
+#pragma unroll
+                        for (int bq = 0; bq < 4; ++bq) {
+                            const int qc = qb + bq;
+                            const int sl = qc == q_lo ? sl_lo : 2 * qc;
+                            const float* pp = L.partial + (size_t)sl * 12 * TM + li;
+#pragma unroll
+                            for (int q = 0; q < NV; ++q) v[bq][q] = qc <= q_hi ? __ldcg(pp + q * TM) : 0.f;
+                        }
+#pragma unroll
+                        for (int bq = 0; bq < 4; ++bq)
+#pragma unroll
+                            for (int q = 0; q < 6; ++q) {
+                                kahan_add(tot[q], cmp[q], v[bq][q]);
+                                if (COMP) kahan_add(tot[q], cmp[q], -v[bq][(6 + q) % NV]);
+                            }
+                    }
                     if (li < T.tn) {
                         const long long gi = (long long)T.t0 + li;
 #pragma unroll
                         for (int q = 0; q < 6; ++q) {
-                            const float v = (float)tot[k][q] * sc.scale;
-                            if (q < 3) L.u[gi * 3 + q] = v; else L.w[gi * 3 + q - 3] = v;
+                            const float val = __fsub_rn(tot[q], cmp[q]) * sc.scale;
+                            if (q < 3) L.u[gi * 3 + q] = val; else L.w[gi * 3 + q - 3] = val;
                         }
                     }
                 }
@@ -321,34 +454,43 @@ mrs_f32_persistent(const MrsLaunch L)
 // Configuration table and dispatch.
 // ---------------------------------------------------------------------------------------------
 const KernelConfig kConfigs[] = {
-    {128, 4}, {128, 2}, {128, 8}, {64, 4}, {256, 2}, {128, 1},
+    {128, 4, 0}, {128, 2, 0}, {128, 8, 0}, {64, 4, 0}, {256, 2, 0}, {128, 1, 0},
+    {128, 2, 1}, {128, 4, 1}, {64, 4, 1}, {256, 2, 1},
 };
 const int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 
-template <int BLOCK, int TPT, bool COMP>
+template <int BLOCK, int TPT, bool COMP, bool PAIRED>
 static cudaError_t launch_t(const MrsLaunch& L, cudaStream_t s)
 {
-    mrs_f32_persistent<BLOCK, TPT, COMP><<<L.P, BLOCK, 0, s>>>(L);
+    mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED><<<L.P, BLOCK, 0, s>>>(L);
     return cudaGetLastError();
 }
 
-template <int BLOCK, int TPT, bool COMP>
+template <int BLOCK, int TPT, bool COMP, bool PAIRED>
 static int occ_t(int* n)
 {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        n, mrs_f32_persistent<BLOCK, TPT, COMP>, BLOCK, 0);
+        n, mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED>, BLOCK, 0);
     return e == cudaSuccess ? MRS_OK : MRS_ECUDA;
 }
 
-#define MRS_DISPATCH(cfg, comp, FN, ...)                                                    \
-    switch (cfg) {                                                                          \
-    case 0: return comp ? FN<128, 4, true>(__VA_ARGS__) : FN<128, 4, false>(__VA_ARGS__);   \
-    case 1: return comp ? FN<128, 2, true>(__VA_ARGS__) : FN<128, 2, false>(__VA_ARGS__);   \
-    case 2: return comp ? FN<128, 8, true>(__VA_ARGS__) : FN<128, 8, false>(__VA_ARGS__);   \
-    case 3: return comp ? FN<64, 4, true>(__VA_ARGS__) : FN<64, 4, false>(__VA_ARGS__);     \
-    case 4: return comp ? FN<256, 2, true>(__VA_ARGS__) : FN<256, 2, false>(__VA_ARGS__);   \
-    case 5: return comp ? FN<128, 1, true>(__VA_ARGS__) : FN<128, 1, false>(__VA_ARGS__);   \
-    default: break;                                                                         \
+#define MRS_CASE(id, B, T, P, FN, ...)                                                    \
+    case id:                                                                              \
+        return comp ? FN<B, T, true, P>(__VA_ARGS__) : FN<B, T, false, P>(__VA_ARGS__);
+
+#define MRS_DISPATCH(cfg, comp, FN, ...)                                                  \
+    switch (cfg) {                                                                        \
+        MRS_CASE(0, 128, 4, false, FN, __VA_ARGS__)                                       \
+        MRS_CASE(1, 128, 2, false, FN, __VA_ARGS__)                                       \
+        MRS_CASE(2, 128, 8, false, FN, __VA_ARGS__)                                       \
+        MRS_CASE(3, 64, 4, false, FN, __VA_ARGS__)                                        \
+        MRS_CASE(4, 256, 2, false, FN, __VA_ARGS__)                                       \
+        MRS_CASE(5, 128, 1, false, FN, __VA_ARGS__)                                       \
+        MRS_CASE(6, 128, 2, true, FN, __VA_ARGS__)                                        \
+        MRS_CASE(7, 128, 4, true, FN, __VA_ARGS__)                                        \
+        MRS_CASE(8, 64, 4, true, FN, __VA_ARGS__)                                         \
+        MRS_CASE(9, 256, 2, true, FN, __VA_ARGS__)                                        \
+    default: break;                                                                       \
     }
 
 cudaError_t launch_mrs_f32(int config, bool comp, const MrsLaunch& L, cudaStream_t s)

@@ -29,7 +29,10 @@ EXPORTS = [
     "mrs_velocity", "mrs_plan_create", "mrs_plan_execute", "mrs_plan_destroy",
     "mrs_plan_config_count", "mrs_plan_config_info", "mrs_plan_info",
     "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run", "mrs_velocity_noalloc",
+    "serve_create", "serve_submit", "serve_poll", "serve_drain", "serve_stats", "serve_destroy",
+    "mrs_autotune", "mrs_autotune_save", "mrs_autotune_load",
 ]
+MRS_JOB_VELOCITY, MRS_JOB_ROD = 0, 1
 
 _vp = ctypes.c_void_p
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -67,6 +70,17 @@ class PararealStats(ctypes.Structure):
                 ("fine_steps", ctypes.c_int64), ("coarse_steps", ctypes.c_int64)]
 
 
+class Job(ctypes.Structure):
+    """``mrs_job``."""
+    _fields_ = [("kind", ctypes.c_int), ("n_points", ctypes.c_int64), ("mu", ctypes.c_double),
+                ("eps", ctypes.c_double), ("X", ctypes.c_void_p), ("f", ctypes.c_void_p),
+                ("n", ctypes.c_void_p), ("u", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("n_rods", ctypes.c_int), ("rod_off", ctypes.POINTER(ctypes.c_int64)),
+                ("Xr", ctypes.c_void_p), ("Dr", ctypes.c_void_p), ("params", RodParams),
+                ("t0", ctypes.c_double), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int),
+                ("scheme", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -100,6 +114,16 @@ def lib():
                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, _vp]
         L.rot_sqrt_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+        L.mrs_autotune.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_double, ctypes.c_double, _dp,
+                                   ctypes.c_int, ctypes.c_int, _ip, ctypes.POINTER(ctypes.c_float)]
+        L.mrs_autotune_save.argtypes = [_vp, ctypes.c_char_p]
+        L.mrs_autotune_load.argtypes = [_vp, ctypes.c_char_p]
+        L.serve_create.argtypes = [ctypes.POINTER(_vp), _vp, ctypes.c_size_t, ctypes.c_int]
+        L.serve_submit.argtypes = [_vp, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]
+        L.serve_poll.argtypes = [_vp, ctypes.c_uint64, _ip, _dp]
+        L.serve_drain.argtypes = [_vp, ctypes.c_double]
+        L.serve_stats.argtypes = [_vp, _i64p, _i64p, _dp, _ip, ctypes.POINTER(ctypes.c_size_t)]
+        L.serve_destroy.argtypes = [_vp]
         L.mrs_velocity_noalloc.argtypes = [ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                            ctypes.c_double, ctypes.c_double, _vp]
         L.parareal_run.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.POINTER(RodParams), _vp,
@@ -217,6 +241,27 @@ class Plan:
             pass
 
 
+def autotune(ctx: Context, offsets, mu, eps, eps_per_sys=None, precision=MRS_F32_COMP, reps=3):
+    """``mrs_autotune``: (best config, its time in ms) for this batch shape."""
+    off, poff = _offsets(offsets)
+    peps = None
+    if eps_per_sys is not None:
+        ev = np.ascontiguousarray(np.asarray(eps_per_sys, dtype=np.float64))
+        peps = ev.ctypes.data_as(_dp)
+    c, ms = ctypes.c_int(), ctypes.c_float()
+    _check(lib().mrs_autotune(ctx.handle, len(off) - 1, poff, float(mu), float(eps), peps,
+                              int(precision), int(reps), ctypes.byref(c), ctypes.byref(ms)))
+    return c.value, ms.value
+
+
+def autotune_save(ctx: Context, path: str):
+    _check(lib().mrs_autotune_save(ctx.handle, path.encode()))
+
+
+def autotune_load(ctx: Context, path: str):
+    _check(lib().mrs_autotune_load(ctx.handle, path.encode()))
+
+
 def plan_config_count() -> int:
     return int(lib().mrs_plan_config_count())
 
@@ -262,3 +307,68 @@ def parareal_run(ctx: Context, rod_off, params: RodParams, X, D, T0, T1, n_slice
         return st
     _check(status)
     return st
+
+
+class Server:
+    """``mrs_server``: continuous batching of velocity and rod jobs on one GPU."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, max_slots: int):
+        self.handle = _vp()
+        self.ctx = ctx
+        self._keep = {}
+        _check(lib().serve_create(ctypes.byref(self.handle), ctx.handle, int(hbm_budget_bytes),
+                                  int(max_slots)))
+
+    def submit_velocity(self, X, f, n, u, w, mu, eps):
+        j = Job()
+        j.kind, j.n_points, j.mu, j.eps = MRS_JOB_VELOCITY, int(X.shape[0]), float(mu), float(eps)
+        j.X, j.f, j.n, j.u, j.w = (t.data_ptr() for t in (X, f, n, u, w))
+        return self._submit(j, (X, f, n, u, w))
+
+    def submit_rod(self, rod_off, X, D, params: RodParams, t0, dt, nsteps, scheme, mu, eps):
+        off, poff = _offsets(rod_off)
+        j = Job()
+        j.kind, j.n_points, j.mu, j.eps = MRS_JOB_ROD, int(X.shape[0]), float(mu), float(eps)
+        j.n_rods, j.rod_off = len(off) - 1, poff
+        j.Xr, j.Dr = X.data_ptr(), D.data_ptr()
+        j.params = params
+        j.t0, j.dt, j.nsteps, j.scheme = float(t0), float(dt), int(nsteps), int(scheme)
+        return self._submit(j, (X, D, off))
+
+    def _submit(self, j, keep):
+        t = ctypes.c_uint64()
+        _check(lib().serve_submit(self.handle, ctypes.byref(j), ctypes.byref(t)))
+        self._keep[t.value] = keep
+        return t.value
+
+    def poll(self, ticket):
+        """(done, latency_s); raises if the job failed."""
+        d, lat = ctypes.c_int(), ctypes.c_double()
+        st = lib().serve_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(d), ctypes.byref(lat))
+        if st == MRS_PENDING:
+            return False, None
+        _check(st)
+        self._keep.pop(ticket, None)
+        return True, lat.value
+
+    def drain(self, timeout_s=600.0):
+        _check(lib().serve_drain(self.handle, float(timeout_s)))
+
+    def stats(self):
+        it, done, peak = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        pairs, pool = ctypes.c_double(), ctypes.c_size_t()
+        _check(lib().serve_stats(self.handle, ctypes.byref(it), ctypes.byref(done),
+                                 ctypes.byref(pairs), ctypes.byref(peak), ctypes.byref(pool)))
+        return {"iterations": it.value, "completed": done.value, "pairs": pairs.value,
+                "peak_active": peak.value, "peak_pool_bytes": pool.value}
+
+    def close(self):
+        if self.handle:
+            _check(lib().serve_destroy(self.handle))
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -17,6 +17,7 @@ same bits.
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 
@@ -28,7 +29,13 @@ EPS_OVER_DS = 1.5           # regularisation eps = 1.5 ds (the paper uses 4 ds; 
 def sinusoid_filament(M: int, L: float = 1.0, A: float = 0.05, lam: float = 1.0):
     """M nodes evenly spaced in arclength on y = A sin(2 pi x / lam), z = 0.
 
-    Returns X[M,3] (float64) and D[M,3,3] with D[k, i] = director D^{i+1}_k."""
+    Returns X[M,3] (float64) and D[M,3,3] with D[k, i] = director D^{i+1}_k (fresh copies)."""
+    X, D = _sinusoid_cached(int(M), float(L), float(A), float(lam))
+    return X.copy(), D.copy()
+
+
+@functools.lru_cache(maxsize=64)
+def _sinusoid_cached(M: int, L: float, A: float, lam: float):
     k = 2.0 * math.pi / lam
     # arclength s(x) on a fine grid (composite trapezoid on 2^20 intervals), then invert
     xmax = L * 1.05 + 1e-3

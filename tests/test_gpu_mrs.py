@@ -98,7 +98,7 @@ def ragged_batch():
     return W.MRSProblem("ragged", off, f32(Xs), f32(fs), f32(ns), eps, 1.3)
 
 
-@pytest.mark.parametrize("config", list(range(6)))
+@pytest.mark.parametrize("config", list(range(10)))
 @pytest.mark.parametrize("precision", [1, 2])
 def test_ragged_batch_every_config(ctx, orc, config, precision):
     p = ragged_batch()
@@ -198,3 +198,28 @@ def test_invalid_arguments_rejected(ctx):
         mrs.mrs_velocity(ctx, [0, 4], X, X, X, u, w, 0.0, 0.1)   # mu = 0
     # empty problem: a no-op
     mrs.mrs_velocity(ctx, [0, 0], X, X, X, u, w, 1.0, 0.1)
+
+
+def test_autotune_picks_a_config_used_by_plans(ctx, orc, tmp_path):
+    """The autotuner times every configuration on the batch shape; a default plan built
+    afterwards uses the winner, the table round-trips through its JSON file, and the tuned
+    plan still matches the oracle."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.batch_systems(seed=66, n_sys=24, lo_exp=8, hi_exp=12)
+    best, ms = mrs.autotune(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32,
+                            reps=2)
+    assert 0 <= best < mrs.plan_config_count() and ms > 0
+    pl = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32)
+    assert pl.info()["config"] == best
+    pl.close()
+    path = str(tmp_path / "tune.json")
+    mrs.autotune_save(ctx, path)
+    c2 = mrs.Context(0)
+    mrs.autotune_load(c2, path)
+    pl = mrs.Plan(c2, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32)
+    assert pl.info()["config"] == best
+    pl.close()
+    c2.close()
+    u, w = run(ctx, p, mrs.MRS_F32)
+    ur, wr = orc.mrs_velocity_batch(p.offsets, p.X, p.f, p.n, 0.0, p.mu, eps_per_sys=p.eps)
+    assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32

@@ -1,0 +1,143 @@
+"""Serving (continuous batching) on the GPU: every job's result is the same alone and in the
+mix, within the float32 tolerance; admission respects slots and the memory pool; results match
+the FP64 oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_12083_gb300 import build as B, mrs
+    B.build()
+    c = mrs.Context(0)
+    yield c
+    c.close()
+
+
+def velocity_job(seed, n_fil, M=256):
+    from paper_2604_12083_gb300 import workloads as W
+    return W.single_system(seed=seed, n_fil=n_fil, M=M, box=4.0)
+
+
+def rod_job(seed, n_rods, M=64):
+    from paper_2604_12083_gb300 import workloads as W
+    return W.rod_system(seed, n_rods, M, box=3.0)
+
+
+def rod_params(eps):
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    c = dict(W.ROD_PLAIN, a=(2e-3,) * 3, b=(20.0,) * 3)
+    return mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"], 1.0, eps)
+
+
+def run_velocity(srv, p):
+    X, f, n = (torch.from_numpy(a).cuda() for a in (p.X, p.f, p.n))
+    u = torch.full_like(X, float("nan"))
+    w = torch.full_like(X, float("nan"))
+    t = srv.submit_velocity(X, f, n, u, w, p.mu, float(p.eps[0]))
+    return t, (X, f, n, u, w)
+
+
+def run_rod(srv, rs, nsteps=12, scheme=1):
+    X = torch.from_numpy(rs.X.copy()).cuda()
+    D = torch.from_numpy(rs.D.copy()).cuda()
+    t = srv.submit_rod(rs.rod_off, X, D, rod_params(rs.eps), 0.0, 2e-6, nsteps, scheme, 1.0, rs.eps)
+    return t, (X, D)
+
+
+def test_results_same_alone_and_in_mix(ctx):
+    from paper_2604_12083_gb300 import mrs
+    import oracle
+    oracle.build()
+    srv = mrs.Server(ctx, 1 << 30, 64)
+    try:
+        pv = velocity_job(90, 5)             # 1280 points
+        pr = rod_job(91, 3)                  # 3 rods x 64 nodes
+        # alone
+        tv, bv = run_velocity(srv, pv)
+        srv.drain()
+        tr, br = run_rod(srv, pr)
+        srv.drain()
+        u_alone, w_alone = bv[3].cpu().numpy(), bv[4].cpu().numpy()
+        X_alone = br[0].cpu().numpy()
+        assert srv.poll(tv)[0] and srv.poll(tr)[0]
+        # in a mix of 24 other jobs of different sizes, all inputs prepared first and then
+        # submitted in one burst so that they are on the GPU together
+        vjobs = [velocity_job(100 + i, 1 + (i % 7)) for i in range(12)]
+        rjobs = [rod_job(200 + i, 1 + (i % 3)) for i in range(12)]
+        torch.cuda.synchronize()
+        others = []
+        for i in range(12):
+            others.append(run_velocity(srv, vjobs[i])[1])
+            others.append(run_rod(srv, rjobs[i], nsteps=3 + i % 5)[1])
+        tv2, bv2 = run_velocity(srv, pv)
+        tr2, br2 = run_rod(srv, pr)
+        srv.drain()
+        st = srv.stats()
+        assert st["peak_active"] >= 6
+        assert rel(bv2[3].cpu().numpy(), u_alone) < TOL32 and rel(bv2[4].cpu().numpy(), w_alone) < TOL32
+        assert rel(br2[0].cpu().numpy() - pr.X, X_alone - pr.X) < 1e-4
+        # and the velocity job matches the FP64 oracle
+        ur, wr = oracle.mrs_velocity(pv.X, pv.f, pv.n, pv.eps[0], pv.mu)
+        assert rel(u_alone, ur) < TOL32 and rel(w_alone, wr) < TOL32
+        # the rod job matches the oracle's RK2 integration
+        op = oracle.RodParams.make(1.0, [2e-3] * 3, [20.0] * 3, 0.05, 2 * np.pi, 2 * np.pi)
+        Xo, _ = oracle.rod_step(pr.rod_off, pr.X, pr.D, op, pr.eps, 1.0, 0.0, 2e-6, 12, oracle.RK2)
+        assert rel(X_alone - pr.X, Xo - pr.X) < 1e-4
+        for b in others:
+            assert all(torch.isfinite(x).all() for x in b[:2])
+        lat = [srv.poll(t)[1] for t in (tv2, tr2)]
+        assert all(l is not None and l > 0 for l in lat)
+    finally:
+        srv.close()
+
+
+def test_admission_by_pool_budget(ctx):
+    """A pool that holds only a few jobs at once: every job still completes, never more
+    admitted than fit."""
+    from paper_2604_12083_gb300 import mrs
+    srv = mrs.Server(ctx, 4 << 20, 64)    # 4 MiB: ~20k point slots
+    try:
+        bufs = []
+        tickets = []
+        for i in range(16):
+            t, b = run_velocity(srv, velocity_job(300 + i, 16))   # 4096 points each
+            tickets.append(t)
+            bufs.append(b)
+        srv.drain()
+        st = srv.stats()
+        assert st["completed"] == 16
+        assert st["peak_active"] <= 5
+        assert st["peak_pool_bytes"] <= 4 << 20
+        for b in bufs:
+            assert torch.isfinite(b[3]).all() and torch.isfinite(b[4]).all()
+    finally:
+        srv.close()
+
+
+def test_invalid_and_oversize_jobs(ctx):
+    from paper_2604_12083_gb300 import mrs
+    srv = mrs.Server(ctx, 2 << 20, 4)
+    try:
+        p = velocity_job(400, 64)       # 16384 points: more than a 2 MiB pool holds
+        with pytest.raises(mrs.MrsError) as e:
+            run_velocity(srv, p)
+        assert e.value.status == mrs.MRS_EBUSY
+        X = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+        D = torch.zeros((4, 3, 3), dtype=torch.float64, device="cuda")
+        with pytest.raises(mrs.MrsError) as e:
+            srv.submit_rod([0, 1, 4], X, D, rod_params(0.01), 0.0, 1e-6, 2, 0, 1.0, 0.01)
+        assert e.value.status == mrs.MRS_EINVAL
+    finally:
+        srv.close()
