@@ -117,24 +117,32 @@ class ClockSampler:
 
 
 def dist_setup():
+    """Rank layout from the torchrun environment; NCCL when a GPU is present, else gloo.  The
+    process group is used only for the timing barrier and the max/sum of two numbers (no
+    data-path collective: every rank runs an independent replica)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
         pg = dist
     return world, rank, local, pg
 
 
 def barrier(pg, dev):
     import torch
-    torch.cuda.synchronize()
+    if dev.type == "cuda":
+        torch.cuda.synchronize()
     if pg is not None:
-        pg.barrier(device_ids=[dev.index])
-    torch.cuda.synchronize()
+        if dev.type == "cuda":
+            pg.barrier(device_ids=[dev.index])
+        else:
+            pg.barrier()
+    if dev.type == "cuda":
+        torch.cuda.synchronize()
 
 
 def max_over_ranks(pg, value, dev):
@@ -153,6 +161,13 @@ def sum_over_ranks(pg, value, dev):
     t = torch.tensor([value], dtype=torch.float64, device=dev)
     pg.all_reduce(t, op=pg.ReduceOp.SUM)
     return float(t.item())
+
+
+def aggregate(pg, dev, step_ms, pairs_per_step, steps):
+    """Whole-job throughput: all ranks' pairs over the slowest rank's timed region."""
+    t_max = max_over_ranks(pg, float(sum(step_ms)), dev)
+    pairs_all = sum_over_ranks(pg, float(pairs_per_step) * steps, dev)
+    return pairs_all / (t_max * 1e-3), t_max / steps
 
 
 def oracle_rate(p, seconds_target, seed=0):
@@ -474,11 +489,7 @@ def run_ours(args, world, rank, local, pg):
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     launch_ms = [a.elapsed_time(b) for a, b in ev]
-    t_ms = sum(launch_ms)
-    t_max = max_over_ranks(pg, t_ms, dev)
-    pairs_all = sum_over_ranks(pg, float(p.pairs) * args.steps, dev)
-    value = pairs_all / (t_max * 1e-3)
-    ms_per_step = t_max / args.steps
+    value, ms_per_step = aggregate(pg, dev, launch_ms, p.pairs, args.steps)
 
     # ---- parity on sampled targets (oracle, rank 0 only; outside the timed region) ----
     rel = None

@@ -50,15 +50,16 @@ int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precisio
 {
     (void)ctx;
     (void)precision;
-    // Measured on GB300 (128-thread packed f32x2 variants are fastest): 256 threads x 2
-    // targets for systems of thousands of points and more, 64 threads x 4 targets (256-target
-    // tiles, less padding and shorter fix-ups) when most points sit in systems below 4096.
+    // Measured on GB300: the packed f32x2 variants are fastest.  256 threads x 2 targets
+    // (512-target tiles) for systems of tens of thousands of points; 256 threads x 1 target with
+    // the source loop unrolled twice (256-target tiles: more tiles, shorter fix-ups, less padding)
+    // when most points sit in systems of at most 8192 points.  mrs_autotune overrides both.
     int64_t small = 0, total = offsets[n_sys];
     for (int s = 0; s < n_sys; ++s) {
         const int64_t ns = offsets[s + 1] - offsets[s];
-        if (ns < 4096) small += ns;
+        if (ns <= 8192) small += ns;
     }
-    if (total > 0 && small * 2 > total) return 8;
+    if (total > 0 && small * 2 > total) return 14;
     return 9;
 }
 

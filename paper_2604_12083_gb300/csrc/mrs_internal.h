@@ -70,6 +70,7 @@ struct KernelConfig {
     int threads;   // threads per CTA
     int tpt;       // targets per thread
     int paired;    // 1: packed f32x2 inner loop (two sources per instruction)
+    int unroll;    // source-loop unroll of the packed loop (independent pair chains in flight)
 };
 
 // Configurations compiled into the library (index = plan config id).

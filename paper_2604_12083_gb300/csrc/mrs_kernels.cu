@@ -184,14 +184,15 @@ __device__ __forceinline__ int cta_of_unit(long long W, int P, long long x)
 }
 
 template <int BLOCK, int TPT>
-struct MinBlocks {
-    static constexpr int value = BLOCK >= 256 ? 2 : (BLOCK >= 128 ? (TPT >= 8 ? 3 : 4) : 8);
+struct MinBlocks {   // CTAs per SM the register allocation must allow
+    static constexpr int value = TPT == 1 ? (BLOCK >= 256 ? 3 : 6)
+                                          : (BLOCK >= 256 ? 2 : (BLOCK >= 128 ? (TPT >= 8 ? 3 : 4) : 8));
 };
 
 // PAIRED: the inner loop runs on packed f32x2 instructions, two sources per instruction
 // (pair_f32x2); sources are then staged structure-of-arrays (nine rows of kChunk floats) so
 // that four consecutive sources of one component are one 16-byte shared load.
-template <int BLOCK, int TPT, bool COMP, bool PAIRED>
+template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, TPT>::value))
 mrs_f32_persistent(const MrsLaunch L)
 {
@@ -291,7 +292,7 @@ mrs_f32_persistent(const MrsLaunch L)
                 for (int k = 0; k < TPT; ++k)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) xn[k][c] = f2(xt[k][c]);
-#pragma unroll 1
+#pragma unroll UNROLL
                 for (int j = 0; j < cntp; j += 4) {
                     float4 v[9];
 #pragma unroll
@@ -454,42 +455,48 @@ mrs_f32_persistent(const MrsLaunch L)
 // Configuration table and dispatch.
 // ---------------------------------------------------------------------------------------------
 const KernelConfig kConfigs[] = {
-    {128, 4, 0}, {128, 2, 0}, {128, 8, 0}, {64, 4, 0}, {256, 2, 0}, {128, 1, 0},
-    {128, 2, 1}, {128, 4, 1}, {64, 4, 1}, {256, 2, 1},
+    {128, 4, 0, 1}, {128, 2, 0, 1}, {128, 8, 0, 1}, {64, 4, 0, 1}, {256, 2, 0, 1}, {128, 1, 0, 1},
+    {128, 2, 1, 1}, {128, 4, 1, 1}, {64, 4, 1, 1}, {256, 2, 1, 1},
+    {256, 2, 1, 2}, {128, 2, 1, 2}, {128, 1, 1, 1}, {128, 1, 1, 2}, {256, 1, 1, 2},
 };
 const int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 
-template <int BLOCK, int TPT, bool COMP, bool PAIRED>
+template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL>
 static cudaError_t launch_t(const MrsLaunch& L, cudaStream_t s)
 {
-    mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED><<<L.P, BLOCK, 0, s>>>(L);
+    mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED, UNROLL><<<L.P, BLOCK, 0, s>>>(L);
     return cudaGetLastError();
 }
 
-template <int BLOCK, int TPT, bool COMP, bool PAIRED>
+template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL>
 static int occ_t(int* n)
 {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        n, mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED>, BLOCK, 0);
+        n, mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED, UNROLL>, BLOCK, 0);
     return e == cudaSuccess ? MRS_OK : MRS_ECUDA;
 }
 
-#define MRS_CASE(id, B, T, P, FN, ...)                                                    \
+#define MRS_CASE(id, B, T, P, U, FN, ...)                                                 \
     case id:                                                                              \
-        return comp ? FN<B, T, true, P>(__VA_ARGS__) : FN<B, T, false, P>(__VA_ARGS__);
+        return comp ? FN<B, T, true, P, U>(__VA_ARGS__) : FN<B, T, false, P, U>(__VA_ARGS__);
 
 #define MRS_DISPATCH(cfg, comp, FN, ...)                                                  \
     switch (cfg) {                                                                        \
-        MRS_CASE(0, 128, 4, false, FN, __VA_ARGS__)                                       \
-        MRS_CASE(1, 128, 2, false, FN, __VA_ARGS__)                                       \
-        MRS_CASE(2, 128, 8, false, FN, __VA_ARGS__)                                       \
-        MRS_CASE(3, 64, 4, false, FN, __VA_ARGS__)                                        \
-        MRS_CASE(4, 256, 2, false, FN, __VA_ARGS__)                                       \
-        MRS_CASE(5, 128, 1, false, FN, __VA_ARGS__)                                       \
-        MRS_CASE(6, 128, 2, true, FN, __VA_ARGS__)                                        \
-        MRS_CASE(7, 128, 4, true, FN, __VA_ARGS__)                                        \
-        MRS_CASE(8, 64, 4, true, FN, __VA_ARGS__)                                         \
-        MRS_CASE(9, 256, 2, true, FN, __VA_ARGS__)                                        \
+        MRS_CASE(0, 128, 4, false, 1, FN, __VA_ARGS__)                                    \
+        MRS_CASE(1, 128, 2, false, 1, FN, __VA_ARGS__)                                    \
+        MRS_CASE(2, 128, 8, false, 1, FN, __VA_ARGS__)                                    \
+        MRS_CASE(3, 64, 4, false, 1, FN, __VA_ARGS__)                                     \
+        MRS_CASE(4, 256, 2, false, 1, FN, __VA_ARGS__)                                    \
+        MRS_CASE(5, 128, 1, false, 1, FN, __VA_ARGS__)                                    \
+        MRS_CASE(6, 128, 2, true, 1, FN, __VA_ARGS__)                                     \
+        MRS_CASE(7, 128, 4, true, 1, FN, __VA_ARGS__)                                     \
+        MRS_CASE(8, 64, 4, true, 1, FN, __VA_ARGS__)                                      \
+        MRS_CASE(9, 256, 2, true, 1, FN, __VA_ARGS__)                                     \
+        MRS_CASE(10, 256, 2, true, 2, FN, __VA_ARGS__)                                    \
+        MRS_CASE(11, 128, 2, true, 2, FN, __VA_ARGS__)                                    \
+        MRS_CASE(12, 128, 1, true, 1, FN, __VA_ARGS__)                                    \
+        MRS_CASE(13, 128, 1, true, 2, FN, __VA_ARGS__)                                    \
+        MRS_CASE(14, 256, 1, true, 2, FN, __VA_ARGS__)                                    \
     default: break;                                                                       \
     }
 

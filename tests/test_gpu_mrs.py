@@ -98,7 +98,7 @@ def ragged_batch():
     return W.MRSProblem("ragged", off, f32(Xs), f32(fs), f32(ns), eps, 1.3)
 
 
-@pytest.mark.parametrize("config", list(range(10)))
+@pytest.mark.parametrize("config", list(range(15)))
 @pytest.mark.parametrize("precision", [1, 2])
 def test_ragged_batch_every_config(ctx, orc, config, precision):
     p = ragged_batch()
@@ -223,3 +223,12 @@ def test_autotune_picks_a_config_used_by_plans(ctx, orc, tmp_path):
     u, w = run(ctx, p, mrs.MRS_F32)
     ur, wr = orc.mrs_velocity_batch(p.offsets, p.X, p.f, p.n, 0.0, p.mu, eps_per_sys=p.eps)
     assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
+
+
+def test_config_table_size(ctx):
+    """Every compiled configuration is covered by the ragged-batch parity test above."""
+    from paper_2604_12083_gb300 import mrs
+    assert mrs.plan_config_count() == 15
+    for c in range(15):
+        info = mrs.plan_config_info(ctx, c)
+        assert info["ctas_per_sm"] >= 1
