@@ -315,37 +315,45 @@ def extra_rod_step(ctx, dev):
 
 
 def extra_parareal(ctx, dev):
-    """8 filaments x 512 nodes, 64 slices, fine RK2 dt = 1e-6, coarse Euler 16 dt, over a
-    shortened horizon (16 fine steps per slice); compared with serial fine RK2 on the GPU."""
+    """8 filaments x 512 nodes, 64 slices, fine RK2 dt = 1e-6 (16 fine steps per slice, a
+    shortened horizon), coarse Euler r dt: serial fine RK2 on the GPU, the regular Parareal
+    schedule and the pipelined one (groups of 8 slices), for r = 4, 8, 16 -- the one-GPU
+    analogue of the paper's regular/pipelined comparison and of its gap-versus-1/r plot."""
     import torch
     from paper_2604_12083_gb300 import mrs, workloads as W
     rs = W.rod_system(4, 8, 512)
     c = W.ROD_PARAREAL
     prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"], 1.0, rs.eps)
-    Ns, nf, r, dt = 64, 16, 16, c["dt"]
+    Ns, nf, dt = 64, 16, c["dt"]
     T1 = Ns * nf * dt
-    Xs, Ds = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
-    mrs.rod_step(ctx, rs.rod_off, prm, Xs, Ds, 0.0, dt, 16, mrs.MRS_RK2)   # warm-up / capture
-    Xs, Ds = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
+    fresh = lambda: (torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev))
+    Xs, Ds = fresh()
+    mrs.rod_step(ctx, rs.rod_off, prm, Xs, Ds, 0.0, dt, 16, mrs.MRS_RK2)   # capture / warm-up
+    Xs, Ds = fresh()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     mrs.rod_step(ctx, rs.rod_off, prm, Xs, Ds, 0.0, dt, Ns * nf, mrs.MRS_RK2)
     torch.cuda.synchronize()
     t_serial = time.perf_counter() - t0
-    Xp, Dp = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
-    st = mrs.parareal_run(ctx, rs.rod_off, prm, Xp, Dp, 0.0, T1, Ns, dt, r, 8, 1e-11,
-                          raise_on_noconv=False)
-    Xp, Dp = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
-    st = mrs.parareal_run(ctx, rs.rod_off, prm, Xp, Dp, 0.0, T1, Ns, dt, r, 8, 1e-11,
-                          raise_on_noconv=False)
-    x0 = rs.X
-    disp_s = Xs.cpu().numpy() - x0
-    disp_p = Xp.cpu().numpy() - x0
-    return {"workload": "8 filaments x 512 nodes, 64 slices x 16 fine RK2 steps (dt=1e-6), coarse 16 dt",
-            "iterations": st.iterations, "increments": [st.incr[i] for i in range(st.iterations)],
-            "parareal_s": st.seconds, "serial_fine_s": t_serial,
-            "fine_steps_executed": st.fine_steps, "serial_fine_steps": Ns * nf,
-            "rel_diff_vs_serial_displacement": float(np.linalg.norm(disp_p - disp_s) / np.linalg.norm(disp_s))}
+    disp_s = Xs.cpu().numpy() - rs.X
+    out = {"workload": "8 filaments x 512 nodes, 64 slices x 16 fine RK2 steps (dt=1e-6), "
+                       "coarse Euler r*dt, tol 1e-11",
+           "serial_fine_s": t_serial, "serial_fine_steps": Ns * nf, "runs": []}
+    for r in (4, 8, 16):
+        for gs in (0, 8):
+            for rep in range(2):          # first run sets up workspaces and graphs
+                Xp, Dp = fresh()
+                st = mrs.parareal_run(ctx, rs.rod_off, prm, Xp, Dp, 0.0, T1, Ns, dt, r, 8, 1e-11,
+                                      raise_on_noconv=False, group_size=gs)
+            disp_p = Xp.cpu().numpy() - rs.X
+            out["runs"].append({
+                "r": r, "schedule": "pipelined (groups of 8)" if gs else "regular",
+                "iterations": st.iterations, "seconds": st.seconds,
+                "increments": [st.incr[i] for i in range(st.iterations)],
+                "fine_steps_executed": st.fine_steps,
+                "rel_diff_vs_serial_displacement": float(np.linalg.norm(disp_p - disp_s) /
+                                                         np.linalg.norm(disp_s))})
+    return out
 
 
 def _serve_jobs(trace, dev, seed):

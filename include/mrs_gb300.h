@@ -184,9 +184,13 @@ typedef struct {
     double wave_f;     /* frequency f */
     double mu;         /* viscosity used by rod_step / parareal_run */
     double eps;        /* MRS regularisation used by rod_step / parareal_run */
+    double lj_eps;     /* Lennard-Jones well depth between rods (Section IV-A); 0 = no repulsion */
+    double lj_sigma;   /* Lennard-Jones length sigma (the paper uses 3 eps); cut at 2^{1/6} sigma */
 } mrs_rod_params;
 
-/* Point force g_k and torque m_k that every node applies to the fluid at time t:
+/* Point force g_k and torque m_k that every node applies to the fluid at time t (plus, when
+ * p->lj_eps > 0, the Lennard-Jones repulsion 24 e [2 (s/r)^12 - (s/r)^6] r_vec / r^2 from every
+ * node of another rod closer than 2^{1/6} s, added to g_k -- reading of Section IV-A):
  * g_k = F_{k+1/2} - F_{k-1/2},  m_k = N_{k+1/2} - N_{k-1/2}
  *        + (1/2)[(X_{k+1}-X_k) x F_{k+1/2} + (X_k-X_{k-1}) x F_{k-1/2}]
  * (the negatives of the fluid-on-rod densities of Eqs. discrete_f / discrete_n times ds),
@@ -241,6 +245,20 @@ MRS_API int parareal_run(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const
                  double* X, double* D, double T0, double T1, int n_slices, double dt_fine,
                  int coarse_ratio, int max_iter, double tol, mrs_parareal_stats* out,
                  void* stream);
+
+/* The pipelined schedule of Section III-A on one GPU: same iteration and same result as
+ * parareal_run, but the slices are cut into groups of group_size consecutive slices whose fine
+ * solves run on their own streams and start as soon as the previous correction sweep has
+ * produced their input states (the sweep streams its results downstream), overlapping the
+ * serial coarse/correction sweep with fine work.  The next iteration's fine solves are queued
+ * before the current increment is known; if the current iteration converges, that work is
+ * discarded.  All ordering is by CUDA events between streams (no device-side waiting).
+ * Arguments, outputs and errors as for parareal_run; group_size in 1..n_slices. */
+MRS_API int parareal_run_pipelined(mrs_ctx* ctx, int n_rods, const int64_t* rod_off,
+                                   const mrs_rod_params* p, double* X, double* D, double T0,
+                                   double T1, int n_slices, double dt_fine, int coarse_ratio,
+                                   int max_iter, double tol, int group_size,
+                                   mrs_parareal_stats* out, void* stream);
 
 /* ==========================================================================================
  * Serving -- continuous batching of pair-sum and rod-integration jobs on one GPU.

@@ -76,6 +76,8 @@ def _bind(L):
                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.c_double, ctypes.c_int, ctypes.c_int]
     L.orc_rodrigues_update.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, _dp]
+    L.orc_lj_forces.argtypes = [ctypes.c_int64, _dp, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
+                                ctypes.c_double, _dp]
     L.orc_num_threads.restype = ctypes.c_int
     return L
 
@@ -200,6 +202,16 @@ def rodrigues_update(D, w, dt, _L=None):
     w, pw = _d(w)
     out = np.zeros_like(D)
     (_L or lib()).orc_rodrigues_update(D.shape[0], pD, pw, float(dt), out.ctypes.data_as(_dp))
+    return out
+
+
+def lj_forces(X, rod_id, sigma, e_lj, F=None, _L=None):
+    """Section IV-A repulsion between nodes of different rods; returns F + the LJ forces."""
+    X, pX = _d(X)
+    rid = np.ascontiguousarray(np.asarray(rod_id, dtype=np.int32))
+    out = np.zeros_like(X) if F is None else np.array(F, dtype=np.float64, copy=True)
+    (_L or lib()).orc_lj_forces(X.shape[0], pX, rid.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                float(sigma), float(e_lj), out.ctypes.data_as(_dp))
     return out
 
 

@@ -346,3 +346,34 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ==========================================================================================
+ * Section IV-A: Lennard-Jones repulsion between swimmers, U(r) = 4 e_lj [(sigma/r)^12 - (sigma/r)^6]
+ * for r < r_c = 2^{1/6} sigma.  Readings: it acts between nodes of different rods only (nodes
+ * of one rod are closer than r_c by construction); the well depth e_lj is its own parameter
+ * (the paper writes it with the MRS symbol epsilon); the potential is cut at its minimum r_c,
+ * so the force is purely repulsive and vanishes continuously at r_c.
+ * Adds F_i = -dU/dx_i = 24 e_lj [2 (sigma/r)^12 - (sigma/r)^6] (x_i - x_j) / r^2 to F[i].
+ * ========================================================================================== */
+void orc_lj_forces(int64_t N, const double* X, const int* rod_id, double sigma, double e_lj,
+                   double* F)
+{
+    const double rc2 = pow(2.0, 1.0 / 3.0) * sigma * sigma;   /* (2^{1/6} sigma)^2 */
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (i = 0; i < N; ++i) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < N; ++j) {
+            if (rod_id[i] == rod_id[j]) continue;
+            double r[3];
+            for (int c = 0; c < 3; ++c) r[c] = X[3*i + c] - X[3*j + c];
+            const double r2 = dot3(r, r);
+            if (r2 >= rc2) continue;
+            const double sr2 = sigma * sigma / r2;
+            const double sr6 = sr2 * sr2 * sr2;
+            const double coef = 24.0 * e_lj * (2.0 * sr6 * sr6 - sr6) / r2;
+            for (int c = 0; c < 3; ++c) acc[c] += coef * r[c];
+        }
+        for (int c = 0; c < 3; ++c) F[3*i + c] += acc[c];
+    }
+}

@@ -176,7 +176,7 @@ struct mrs_ctx {
     size_t plan_cache_max = 16;
     // rod workspaces used by rod_forces / rod_step / parareal_run (LRU, most recent first)
     std::list<mrs::RodWorkspace*> rod_ws;
-    size_t rod_ws_max = 96;
+    size_t rod_ws_max = 256;
     // measured best kernel configurations (mrs_autotune)
     std::vector<mrs::TuneEntry> tuned;
 };

@@ -93,6 +93,15 @@ __global__ void parareal_correct_kernel(int N1, const double* __restrict__ FpX,
     atomic_max_nonneg(incr, den > 0.0 ? sqrt(num / den) : sqrt(num));
 }
 
+cudaError_t launch_parareal_correct(int N1, const double* FpX, const double* FpD, const double* GnX,
+                                    const double* GnD, double* GoX, double* GoD, double* UX,
+                                    double* UD, double* incr, cudaStream_t s)
+{
+    parareal_correct_kernel<<<(N1 + 127) / 128, 128, 0, s>>>(N1, FpX, FpD, GnX, GnD, GoX, GoD, UX, UD,
+                                                             (unsigned long long*)incr);
+    return cudaGetLastError();
+}
+
 }  // namespace mrs
 
 using namespace mrs;
@@ -163,8 +172,7 @@ extern "C" int parareal_run(mrs_ctx* ctx, int n_rods, const int64_t* rod_off,
     long long fine_steps = 0, coarse_steps = 0;
     // coarse propagation of the work state (WX, WD) over slice n (from T_{n-1})
     auto coarse = [&](int n) -> int {
-        const double t = T0 + (n - 1) * dT;
-        int r = rod_ws_set_times(wsG, &t, s);
+        int r = rod_ws_set_times(wsG, T0 + (n - 1) * dT, 0.0, s);
         if (r) return r;
         coarse_steps += n_coarse;
         return rod_ws_steps(wsG, p, WX.p, WD.p, dt_coarse, n_coarse, MRS_EULER, s);
@@ -197,9 +205,7 @@ extern "C" int parareal_run(mrs_ctx* ctx, int n_rods, const int64_t* rod_off,
         if ((st = cpy(FX.p, UX.p + (k - 1) * sx, sx * n_open)) ||
             (st = cpy(FD.p, UD.p + (k - 1) * sd, sd * n_open)))
             return st;
-        std::vector<double> t0s(n_open);
-        for (int i = 0; i < n_open; ++i) t0s[i] = T0 + (k - 1 + i) * dT;
-        if ((st = rod_ws_set_times(wsF, t0s.data(), s))) return st;
+        if ((st = rod_ws_set_times(wsF, T0 + (k - 1) * dT, dT, s))) return st;
         if ((st = rod_ws_steps(wsF, p, FX.p, FD.p, dt_fine, (int)n_fine, MRS_RK2, s))) return st;
         fine_steps += n_fine * n_open;
         MRS_CHECK_CUDA(cudaMemsetAsync(INC.p, 0, sizeof(double), s));

@@ -60,12 +60,14 @@ void rod_ws_free(RodWorkspace* ws)
 }
 
 int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int precision,
-               double mu, double eps, RodWorkspace** out)
+               double mu, double eps, RodWorkspace** out, int tag)
 {
     *out = nullptr;
     for (auto it = ctx->rod_ws.begin(); it != ctx->rod_ws.end(); ++it) {
         RodWorkspace* ws = *it;
-        if (ws->n_inst != n_inst || ws->n_rods != n_rods || ws->precision != precision) continue;
+        if (ws->n_inst != n_inst || ws->n_rods != n_rods || ws->precision != precision ||
+            ws->tag != tag)
+            continue;
         if (std::memcmp(ws->rod_off.data(), rod_off, sizeof(int64_t) * (n_rods + 1)) != 0) continue;
         if ((eps > 0.0) != (ws->plan != nullptr)) continue;
         if (ws->plan && (ws->plan->mu != mu || ws->plan->eps[0] != eps)) continue;
@@ -77,6 +79,7 @@ int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int
     RodWorkspace* ws = new RodWorkspace();
     ws->ctx = ctx;
     ws->n_inst = n_inst;
+    ws->tag = tag;
     ws->n_rods = n_rods;
     ws->precision = precision;
     ws->rod_off.assign(rod_off, rod_off + n_rods + 1);
@@ -154,11 +157,9 @@ RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt)
     return L;
 }
 
-int rod_ws_set_times(RodWorkspace* ws, const double* t0_host, cudaStream_t s)
+int rod_ws_set_times(RodWorkspace* ws, double t_first, double dT, cudaStream_t s)
 {
-    MRS_CHECK_CUDA(cudaMemcpyAsync(ws->d_t0, t0_host, sizeof(double) * ws->n_inst,
-                                   cudaMemcpyHostToDevice, s));
-    MRS_CHECK_CUDA(cudaMemsetAsync(ws->d_step, 0, sizeof(long long), s));
+    MRS_CHECK_CUDA(launch_set_times(ws->d_t0, ws->n_inst, t_first, dT, ws->d_step, s));
     return MRS_OK;
 }
 
@@ -305,8 +306,7 @@ int rod_forces(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_p
     if ((st = rod_ws_get(ctx, n_rods, rod_off, 1, MRS_F64, 0.0, 0.0, &ws))) return st;
     const RodLaunch L = rod_launch(ws, p, 0.0);
     cudaStream_t s = (cudaStream_t)stream;
-    const double zero = 0.0;
-    if ((st = rod_ws_set_times(ws, &zero, s))) return st;
+    if ((st = rod_ws_set_times(ws, 0.0, 0.0, s))) return st;
     cudaError_t e = launch_rod_forces(L, X, D, t, g, m, nullptr, nullptr, nullptr, s);
     if (e != cudaSuccess) {
         set_error("rod force kernels failed: %s", cudaGetErrorString(e));
@@ -335,7 +335,7 @@ int rod_step(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_par
     RodWorkspace* ws = nullptr;
     if ((st = rod_ws_get(ctx, n_rods, rod_off, 1, mrs_precision, p->mu, p->eps, &ws))) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = rod_ws_set_times(ws, &t0, s))) return st;
+    if ((st = rod_ws_set_times(ws, t0, 0.0, s))) return st;
     return rod_ws_steps(ws, p, X, D, dt, nsteps, scheme, s);
 }
 

@@ -26,12 +26,15 @@ cudaError_t launch_rod_update64(const RodLaunch& L, const double* X0, const doub
                                 const double* u, const double* w, double h, double* X1,
                                 double* D1, bool bump_step, cudaStream_t s);
 cudaError_t launch_rot_sqrt_batch(int n, const double* R, double* S, cudaStream_t s);
+cudaError_t launch_set_times(double* t0, int n_inst, double t_first, double dT, long long* step,
+                             cudaStream_t s);
 
 // One batch of n_inst identical rod sets (instance i = the rods of rod_off shifted by i*N1
 // nodes); every instance is its own hydrodynamic system.
 struct RodWorkspace {
     mrs_ctx* ctx = nullptr;
     int n_inst = 0;
+    int tag = 0;               // distinguishes workspaces used concurrently for the same shape
     int n_rods = 0;            // rods per instance
     int N1 = 0;                // nodes per instance
     int N = 0;                 // total nodes
@@ -67,13 +70,18 @@ struct RodWorkspace {
 };
 
 int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int precision,
-               double mu, double eps, RodWorkspace** out);
+               double mu, double eps, RodWorkspace** out, int tag = 0);
+// Parareal correction of one slice (see parareal.cu); GnX == NULL accepts the fine value.
+cudaError_t launch_parareal_correct(int N1, const double* FpX, const double* FpD, const double* GnX,
+                                    const double* GnD, double* GoX, double* GoD, double* UX,
+                                    double* UD, double* incr, cudaStream_t s);
 void rod_ws_free(RodWorkspace* ws);
 RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt);
 // Enqueue `nsteps` steps of size dt on the workspace's state buffers X, D (device), with the
 // instance start times already set; replays captured graphs.
 int rod_ws_steps(RodWorkspace* ws, const mrs_rod_params* p, double* X, double* D, double dt,
                  int nsteps, int scheme, cudaStream_t s);
-int rod_ws_set_times(RodWorkspace* ws, const double* t0_host, cudaStream_t s);
+// Instance i of the batch starts at t_first + i * dT; resets the step counter (stream-ordered).
+int rod_ws_set_times(RodWorkspace* ws, double t_first, double dT, cudaStream_t s);
 
 }  // namespace mrs

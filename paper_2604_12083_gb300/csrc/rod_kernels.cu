@@ -242,7 +242,89 @@ __global__ void rod_update_kernel(const RodLaunch L, const double* X0, const dou
     for (int q = 0; q < 9; ++q) D1[9 * (size_t)k + q] = Dn[q];
 }
 
+// Start times of the instances of a batch, t0[i] = t_first + i * dT, and the step counter reset:
+// a kernel rather than a host copy so that enqueueing never waits for the stream.
+__global__ void rod_set_times_kernel(double* t0, int n_inst, double t_first, double dT,
+                                     long long* step)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *step = 0;
+    if (i < n_inst) t0[i] = t_first + (double)i * dT;
+}
+
+// Section IV-A: Lennard-Jones repulsion U = 4 e [(s/r)^12 - (s/r)^6] for r < r_c = 2^{1/6} s
+// between nodes of different rods of the same instance, added to the force each node applies to
+// the fluid (the rod is massless: elastic + LJ + fluid force = 0 on every node).  Every pair is
+// screened in float32 against r_c^2 with a 1 % margin (the screen only has to be conservative);
+// the rare close pairs are evaluated in float64 from the float64 positions.  Two nodes belong to
+// the same rod when their rods start at the same node (node index minus index within the rod).
+constexpr int kLJTile = 256;
+
+__global__ void rod_lj_kernel(const RodLaunch L, const double* __restrict__ X, double* g64, float* gf)
+{
+    __shared__ float sx[kLJTile * 3];
+    __shared__ int skey[kLJTile];
+    const int inst = blockIdx.y;
+    const int N1 = L.nodes_per_inst;
+    const int kl = blockIdx.x * kLJTile + threadIdx.x;
+    const bool valid = kl < N1;
+    const long long k = (long long)inst * N1 + (valid ? kl : N1 - 1);
+    const double xi = X[3 * k], yi = X[3 * k + 1], zi = X[3 * k + 2];
+    const float xf = (float)xi, yf = (float)yi, zf = (float)zi;
+    const int key = (int)k - L.node_info[k].x;
+    const double s2 = L.p.lj_sigma * L.p.lj_sigma;
+    const double rc2 = 1.2599210498948732 * s2;            // (2^{1/6} sigma)^2
+    const float rc2f = (float)(1.01 * rc2);
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    for (int j0 = 0; j0 < N1; j0 += kLJTile) {
+        const int cnt = min(kLJTile, N1 - j0);
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            const long long j = (long long)inst * N1 + j0 + threadIdx.x;
+            sx[3 * threadIdx.x] = (float)X[3 * j];
+            sx[3 * threadIdx.x + 1] = (float)X[3 * j + 1];
+            sx[3 * threadIdx.x + 2] = (float)X[3 * j + 2];
+            skey[threadIdx.x] = (int)j - L.node_info[j].x;
+        }
+        __syncthreads();
+        for (int t = 0; t < cnt; ++t) {
+            const float dx = xf - sx[3 * t], dy = yf - sx[3 * t + 1], dz = zf - sx[3 * t + 2];
+            const float r2f = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2f < rc2f && skey[t] != key) {
+                const long long j = (long long)inst * N1 + j0 + t;
+                const double rx = xi - X[3 * j], ry = yi - X[3 * j + 1], rz = zi - X[3 * j + 2];
+                const double r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 < rc2 && r2 > 0.0) {
+                    const double sr2 = s2 / r2, sr6 = sr2 * sr2 * sr2;
+                    const double c = 24.0 * L.p.lj_eps * (2.0 * sr6 * sr6 - sr6) / r2;
+                    acc0 += c * rx;
+                    acc1 += c * ry;
+                    acc2 += c * rz;
+                }
+            }
+        }
+    }
+    if (!valid) return;
+    if (g64) {
+        g64[3 * k] += acc0;
+        g64[3 * k + 1] += acc1;
+        g64[3 * k + 2] += acc2;
+    }
+    if (gf) {
+        gf[3 * k] = (float)((double)gf[3 * k] + acc0);
+        gf[3 * k + 1] = (float)((double)gf[3 * k + 1] + acc1);
+        gf[3 * k + 2] = (float)((double)gf[3 * k + 2] + acc2);
+    }
+}
+
 static inline int nblk(int n, int b) { return (n + b - 1) / b; }
+
+cudaError_t launch_set_times(double* t0, int n_inst, double t_first, double dT, long long* step,
+                             cudaStream_t s)
+{
+    rod_set_times_kernel<<<nblk(n_inst, 128), 128, 0, s>>>(t0, n_inst, t_first, dT, step);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double* D, double t_off,
                               double* g64, double* m64, float* Xf, float* gf, float* mf,
@@ -251,6 +333,10 @@ cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double*
     if (L.N == 0) return cudaSuccess;
     rod_segment_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, D, t_off);
     rod_node_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, g64, m64, Xf, gf, mf);
+    if (L.p.lj_eps > 0.0) {
+        const dim3 grid(nblk(L.nodes_per_inst, kLJTile), L.N / L.nodes_per_inst);
+        rod_lj_kernel<<<grid, kLJTile, 0, s>>>(L, X, g64, gf);
+    }
     return cudaGetLastError();
 }
 

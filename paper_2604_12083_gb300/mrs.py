@@ -30,7 +30,7 @@ EXPORTS = [
     "mrs_plan_config_count", "mrs_plan_config_info", "mrs_plan_info",
     "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run", "mrs_velocity_noalloc",
     "serve_create", "serve_submit", "serve_poll", "serve_drain", "serve_stats", "serve_destroy",
-    "mrs_autotune", "mrs_autotune_save", "mrs_autotune_load",
+    "mrs_autotune", "mrs_autotune_save", "mrs_autotune_load", "parareal_run_pipelined",
 ]
 MRS_JOB_VELOCITY, MRS_JOB_ROD = 0, 1
 
@@ -50,16 +50,19 @@ class RodParams(ctypes.Structure):
     """``mrs_rod_params``."""
     _fields_ = [("L", ctypes.c_double), ("a", ctypes.c_double * 3), ("b", ctypes.c_double * 3),
                 ("wave_A", ctypes.c_double), ("wave_k", ctypes.c_double),
-                ("wave_f", ctypes.c_double), ("mu", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("wave_f", ctypes.c_double), ("mu", ctypes.c_double), ("eps", ctypes.c_double),
+                ("lj_eps", ctypes.c_double), ("lj_sigma", ctypes.c_double)]
 
     @classmethod
-    def make(cls, L, a, b, wave_A, wave_k, wave_f, mu, eps):
+    def make(cls, L, a, b, wave_A, wave_k, wave_f, mu, eps, lj_eps=0.0, lj_sigma=None):
         p = cls()
         p.L = L
         for q in range(3):
             p.a[q] = a[q]
             p.b[q] = b[q]
         p.wave_A, p.wave_k, p.wave_f, p.mu, p.eps = wave_A, wave_k, wave_f, mu, eps
+        p.lj_eps = lj_eps
+        p.lj_sigma = 3.0 * eps if lj_sigma is None else lj_sigma
         return p
 
 
@@ -114,6 +117,11 @@ def lib():
                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, _vp]
         L.rot_sqrt_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+        L.parareal_run_pipelined.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.POINTER(RodParams),
+                                             _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                             ctypes.POINTER(PararealStats), _vp]
         L.mrs_autotune.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_double, ctypes.c_double, _dp,
                                    ctypes.c_int, ctypes.c_int, _ip, ctypes.POINTER(ctypes.c_float)]
         L.mrs_autotune_save.argtypes = [_vp, ctypes.c_char_p]
@@ -295,14 +303,21 @@ def rot_sqrt_batch(ctx: Context, R, S, stream=None):
 
 
 def parareal_run(ctx: Context, rod_off, params: RodParams, X, D, T0, T1, n_slices, dt_fine,
-                 coarse_ratio, max_iter, tol, stream=None, raise_on_noconv=True):
-    """``parareal_run``: Parareal in place on device float64 X, D; returns the statistics."""
+                 coarse_ratio, max_iter, tol, stream=None, raise_on_noconv=True, group_size=0):
+    """``parareal_run`` (group_size 0) or ``parareal_run_pipelined`` (group_size >= 1): Parareal
+    in place on device float64 X, D; returns the statistics."""
     off, poff = _offsets(rod_off)
     st = PararealStats()
-    status = lib().parareal_run(ctx.handle, len(off) - 1, poff, ctypes.byref(params), _ptr(X),
-                                _ptr(D), float(T0), float(T1), int(n_slices), float(dt_fine),
-                                int(coarse_ratio), int(max_iter), float(tol), ctypes.byref(st),
-                                _stream(stream))
+    if group_size:
+        status = lib().parareal_run_pipelined(
+            ctx.handle, len(off) - 1, poff, ctypes.byref(params), _ptr(X), _ptr(D), float(T0),
+            float(T1), int(n_slices), float(dt_fine), int(coarse_ratio), int(max_iter),
+            float(tol), int(group_size), ctypes.byref(st), _stream(stream))
+    else:
+        status = lib().parareal_run(ctx.handle, len(off) - 1, poff, ctypes.byref(params), _ptr(X),
+                                    _ptr(D), float(T0), float(T1), int(n_slices), float(dt_fine),
+                                    int(coarse_ratio), int(max_iter), float(tol), ctypes.byref(st),
+                                    _stream(stream))
     if status == MRS_ENOCONV and not raise_on_noconv:
         return st
     _check(status)

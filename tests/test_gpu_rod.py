@@ -182,3 +182,58 @@ def test_rod_invalid_arguments(ctx):
         mrs.rod_step(ctx, [0, 4], gp, X, D, 0.0, -1.0, 1, 0)          # dt < 0
     with pytest.raises(mrs.MrsError):
         mrs.parareal_run(ctx, [0, 4], gp, X, D, 0.0, 1e-3, 3, 1e-4, 4, 3, 1e-9)  # ragged slices
+
+
+@pytest.mark.parametrize("group_size", [1, 2, 4])
+def test_pipelined_parareal_equals_regular(ctx, group_size):
+    """Same iteration, different schedule: the pipelined run reaches the regular run's result
+    (up to float32 rounding of the pair sums, whose batches are cut differently) in the same
+    number of iterations."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(75, 2, 24, box=1.5)
+    cfg = dict(W.WAVE, a=(2e-3,) * 3, b=(0.3,) * 3)
+    gp, _ = params(cfg, rs.eps)
+    Ns, dt, r = 8, 5e-5, 4
+    T1 = Ns * 16 * dt
+    res = {}
+    for gs in (0, group_size):
+        Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+        st = mrs.parareal_run(ctx, rs.rod_off, gp, Xd, Dd, 0.0, T1, Ns, dt, r, Ns, 1e-10,
+                              group_size=gs)
+        res[gs] = (Xd.cpu().numpy(), Dd.cpu().numpy(), st)
+    (Xa, Da, sa), (Xb, Db, sb) = res[0], res[group_size]
+    assert rel(Xb - rs.X, Xa - rs.X) < 1e-5
+    assert np.abs(np.einsum("kir,kjr->kij", Db, Db) - np.eye(3)).max() < 1e-12
+    assert abs(sa.iterations - sb.iterations) <= 1
+    assert abs(sa.incr[0] - sb.incr[0]) <= 1e-3 * sa.incr[0]
+
+
+def test_rod_forces_with_lj_match_oracle(ctx, orc):
+    """Two rods crossing within the Lennard-Jones cut-off: g = elastic + LJ force (Section IV-A)."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    M = 40
+    X1, D1 = W.sinusoid_filament(M)
+    X2, D2 = W.sinusoid_filament(M)
+    Q = np.array([[0.0, 0.0, 1.0], [0.0, 1.0, 0.0], [-1.0, 0.0, 0.0]])   # rod 2 rotated and shifted
+    X2 = X2 @ Q.T + np.array([0.5, 0.0, 0.004])
+    D2 = np.einsum("rc,kic->kir", Q, D2)
+    X = np.concatenate([X1, X2])
+    D = np.concatenate([D1, D2])
+    off = np.array([0, M, 2 * M], np.int64)
+    eps = 1.5 / (M - 1)
+    cfg = dict(W.ROD_PLAIN)
+    gp = mrs.RodParams.make(cfg["L"], cfg["a"], cfg["b"], cfg["wave_A"], cfg["wave_k"],
+                            cfg["wave_f"], 1.0, eps, lj_eps=0.05)
+    op = orc.RodParams.make(cfg["L"], cfg["a"], cfg["b"], cfg["wave_A"], cfg["wave_k"], cfg["wave_f"])
+    Xd, Dd = torch.from_numpy(X).cuda(), torch.from_numpy(D).cuda()
+    g = torch.empty_like(Xd)
+    m = torch.empty_like(Xd)
+    mrs.rod_forces(ctx, off, gp, Xd, Dd, 0.2, g, m)
+    torch.cuda.synchronize()
+    go, mo = orc.rod_forces(off, X, D, op, 0.2)
+    rid = np.repeat([0, 1], M)
+    lj = orc.lj_forces(X, rid, gp.lj_sigma, gp.lj_eps)
+    assert np.abs(lj).max() > 1e-3 * np.abs(go).max()       # the rods do touch
+    ref = go + lj
+    assert np.abs(g.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert np.abs(m.cpu().numpy() - mo).max() <= 1e-11 * np.abs(mo).max()

@@ -191,3 +191,48 @@ def test_convergence_order(orc, scheme, order):
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     target = 2.0**order
     assert abs(r1 - target) < 0.25 * target and abs(r2 - target) < 0.2 * target, (errs, r1, r2)
+
+
+def _lj_energy(X, rod_id, sigma, e_lj):
+    """Total cut LJ energy over pairs of nodes on different rods (independent of the oracle)."""
+    rc = 2.0 ** (1.0 / 6.0) * sigma
+    E = 0.0
+    for i in range(len(X)):
+        for j in range(i + 1, len(X)):
+            if rod_id[i] == rod_id[j]:
+                continue
+            r = np.linalg.norm(X[i] - X[j])
+            if r < rc:
+                E += 4 * e_lj * ((sigma / r) ** 12 - (sigma / r) ** 6) + e_lj   # shifted: 0 at r_c
+    return E
+
+
+def test_lj_force_is_minus_energy_gradient(orc):
+    rng = np.random.default_rng(48)
+    X = rng.uniform(0, 0.6, (30, 3))
+    rid = np.repeat(np.arange(6), 5)
+    sigma, e_lj = 0.12, 0.7
+    F = orc.lj_forces(X, rid, sigma, e_lj)
+    h = 1e-7
+    for i in range(len(X)):
+        for c in range(3):
+            Xp = X.copy()
+            Xp[i, c] += h
+            Xm = X.copy()
+            Xm[i, c] -= h
+            dE = (_lj_energy(Xp, rid, sigma, e_lj) - _lj_energy(Xm, rid, sigma, e_lj)) / (2 * h)
+            assert abs(-dE - F[i, c]) <= 1e-5 * max(1.0, np.abs(F).max())
+    assert np.abs(F.sum(axis=0)).max() <= 1e-10 * np.abs(F).max()          # action = reaction
+    assert np.abs(F).max() > 0
+
+
+def test_lj_cut_and_same_rod_exclusion(orc):
+    sigma = 0.1
+    rc = 2.0 ** (1.0 / 6.0) * sigma
+    X = np.array([[0.0, 0, 0], [rc * (1 + 1e-9), 0, 0], [0.0, 0.5 * sigma, 0]])
+    F = orc.lj_forces(X, [0, 1, 0], sigma, 1.0)
+    assert np.all(F == 0.0)          # beyond r_c, or on the same rod
+    # just inside r_c the force is tiny (continuous at the cut), and repulsive
+    X[1, 0] = rc * (1 - 1e-6)
+    F = orc.lj_forces(X, [0, 1, 0], sigma, 1.0)
+    assert F[1, 0] > 0 and F[1, 0] < 1e-3
