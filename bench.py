@@ -30,7 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_PAIR = 92          # canonical algorithmic flop count of one ordered pair
-METRIC = "MRS pair-interactions/s"
+METRIC = ("MRS pair-interactions/s (frac of FP32 peak) at 1e-5 rel err; "
+          "p50/p99 solve latency")
 UNIT = "pairs/s"
 
 
@@ -455,6 +456,59 @@ def run_extras(ctx, dev):
     return out
 
 
+def run_rod_kernels(args):
+    """Rod force assembly (segment + node kernels) and the explicit update on 1024 rods x 1024
+    nodes (1,048,576 nodes, float64 state): achieved bytes per second against the measured HBM
+    copy bandwidth.  Algorithmic bytes per node: forces read X, D (96 B) and write g, m (48 B);
+    the update reads X, D and u, w (float32, 24 B) and writes X, D (96 B)."""
+    import torch
+    from paper_2604_12083_gb300 import build as B, mrs, workloads as W
+    B.build()
+    dev = torch.device("cuda", 0)
+    ctx = mrs.Context(0)
+    rs = W.rod_system(21, 1024, 1024, box=60.0)
+    c = W.ROD_PLAIN
+    prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"], 1.0, rs.eps)
+    X = torch.from_numpy(rs.X).to(dev)
+    D = torch.from_numpy(rs.D).to(dev)
+    g = torch.empty_like(X)
+    m = torch.empty_like(X)
+    u = (torch.randn(X.shape, device=dev) * 1e-3).float()
+    w = (torch.randn(X.shape, device=dev) * 1e-2).float()
+    N = X.shape[0]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        tot = 0.0
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    reps = max(3, min(args.steps, 50))
+    t_f = timed(lambda: mrs.rod_forces(ctx, rs.rod_off, prm, X, D, 0.1, g, m), reps)
+    t_a = timed(lambda: mrs.rod_advance(ctx, X, D, u, w, 1e-7), reps)
+    peak = float(load_peaks().get("hbm_gbs", 6800.0))
+    fb, ab = 144 * N, 216 * N
+    line = {"case": "rod_kernels", "workload": "1024 rods x 1024 nodes (1,048,576 nodes), float64",
+            "rod_forces": {"ms": t_f, "algorithmic_bytes": fb, "achieved_gbs": fb / (t_f * 1e-3) / 1e9,
+                           "frac_of_hbm": fb / (t_f * 1e-3) / 1e9 / peak,
+                           "kernels": "rod_segment_kernel + rod_node_kernel"},
+            "rod_advance": {"ms": t_a, "algorithmic_bytes": ab, "achieved_gbs": ab / (t_a * 1e-3) / 1e9,
+                            "frac_of_hbm": ab / (t_a * 1e-3) / 1e9 / peak, "kernels": "rod_update_kernel"},
+            "peak_hbm_gbs": peak, "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
     from paper_2604_12083_gb300 import build as B, mrs, workloads as W
@@ -578,8 +632,15 @@ def run_ours(args, world, rank, local, pg):
         line["cpu_baseline"] = {"value": nt * p.n_points / dt, "unit": UNIT,
                                 "cores": oracle.num_threads(), "kind": "oracle",
                                 "sample": "%d sampled targets x %d sources (FP64)" % (nt, p.n_points)}
+    line["frac_of_fp32_peak"] = line["roofline"]["frac"]
     if rank == 0 and args.extras:
         line["extras"] = run_extras(ctx, dev)
+        nominal = line["extras"].get("serve", {}).get("nominal_2000_per_s", {}).get("served")
+        if nominal:
+            line["p50_latency_s"] = nominal["p50_latency_s"]
+            line["p99_latency_s"] = nominal["p99_latency_s"]
+            line["latency_workload"] = ("served jobs, Poisson 2000 req/s, 70 % pair sums / 30 % "
+                                        "100-step rod integrations, N log-uniform [1k, 64k]")
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -593,6 +654,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--case", choices=["main", "rod_kernels"], default="main",
+                    help="rod_kernels: time the rod force and update kernels on 1M nodes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -601,6 +664,9 @@ def main():
         world = int(os.environ.get("WORLD_SIZE", "1"))
         rank = int(os.environ.get("RANK", "0"))
         run_reference(args, world, rank)
+        return
+    if args.case == "rod_kernels":
+        run_rod_kernels(args)
         return
     world, rank, local, pg = dist_setup()
     run_ours(args, world, rank, local, pg)

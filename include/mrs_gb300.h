@@ -202,6 +202,13 @@ typedef struct {
 MRS_API int rod_forces(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_params* p,
                const double* X, const double* D, double t, double* g, double* m, void* stream);
 
+/* One explicit update (Eqs. newx, newD) with given velocities: X_k += u_k dt and every director
+ * of node k rotated by |w_k| dt about w_k (unchanged where w_k = 0), in place.
+ *   X, D   device float64 [N][3], [N][3][3];  u, w  device [N][3], float32 (vel_f64 = 0) or
+ *   float64 (vel_f64 = 1).  Errors: MRS_EINVAL, MRS_ECUDA. */
+MRS_API int rod_advance(mrs_ctx* ctx, int64_t N, double* X, double* D, const void* u, const void* w,
+                        double dt, int vel_f64, void* stream);
+
 /* nsteps explicit time steps of all rods as ONE hydrodynamic system (every node is a source
  * for every node), in place on device float64 X[N][3], D[N][3][3], from time t0 with step dt.
  * Each stage: rod_forces -> float32 pack -> MRS pair sum (mrs_precision) -> float64 update
@@ -219,6 +226,16 @@ MRS_API int rod_step(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs
  * quaternion (1+q)/|1+q|; at an angle of exactly pi either quarter turn is returned.
  * Errors: MRS_EINVAL, MRS_ECUDA. */
 MRS_API int rot_sqrt_batch(mrs_ctx* ctx, int n, const double* R, double* S, void* stream);
+
+/* Checkpoint / resume of a rod system (no counterpart in the paper; Parareal slice states and
+ * long runs restart from one).  Saves t, the rod offsets, X [N][3] and D [N][3][3] (float64,
+ * device or host pointers) with a hash; load checks magic, version, sizes, offsets and hash
+ * before writing X, D (device or host) and *t.  Both synchronize `stream`.
+ * Errors: MRS_EINVAL (I/O, mismatch, corruption), MRS_ECUDA. */
+MRS_API int rod_checkpoint_save(const char* path, int n_rods, const int64_t* rod_off,
+                                const double* X, const double* D, double t, void* stream);
+MRS_API int rod_checkpoint_load(const char* path, int n_rods, const int64_t* rod_off, double* X,
+                                double* D, double* t, void* stream);
 
 /* ==========================================================================================
  * Parareal -- Section II-D, Eqs. (initial), (intermediate), (serial_correct); Eq. (true_err).

@@ -339,6 +339,31 @@ int rod_step(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_par
     return rod_ws_steps(ws, p, X, D, dt, nsteps, scheme, s);
 }
 
+int rod_advance(mrs_ctx* ctx, int64_t N, double* X, double* D, const void* u, const void* w,
+                double dt, int vel_f64, void* stream)
+{
+    clear_error();
+    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+    MRS_REQUIRE(N >= 0 && N < (1LL << 30), "N out of range");
+    MRS_REQUIRE(std::isfinite(dt), "dt must be finite");
+    if (N == 0) return MRS_OK;
+    MRS_REQUIRE(X && D && u && w, "NULL pointer");
+    MRS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    RodLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.N = (int)N;
+    L.nodes_per_inst = (int)N;
+    cudaError_t e = vel_f64 ? launch_rod_update64(L, X, D, (const double*)u, (const double*)w, dt, X, D,
+                                                  false, (cudaStream_t)stream)
+                            : launch_rod_update(L, X, D, (const float*)u, (const float*)w, dt, X, D, false,
+                                                (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error("rod update kernel failed: %s", cudaGetErrorString(e));
+        return MRS_ECUDA;
+    }
+    return MRS_OK;
+}
+
 int rot_sqrt_batch(mrs_ctx* ctx, int n, const double* R, double* S, void* stream)
 {
     clear_error();

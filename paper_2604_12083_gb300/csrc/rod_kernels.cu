@@ -123,7 +123,8 @@ __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__
         for (int r = 0; r < 3; ++r)
             Dh[3 * i + r] = S[3 * r] * Dk[3 * i] + S[3 * r + 1] * Dk[3 * i + 1] + S[3 * r + 2] * Dk[3 * i + 2];
     const double* Xk = X + 3 * (size_t)k;
-    const double e[3] = {(Xk[3] - Xk[0]) / ds, (Xk[4] - Xk[1]) / ds, (Xk[5] - Xk[2]) / ds};
+    const double ids = 1.0 / ds;   // one division; float64 divisions are expensive here
+    const double e[3] = {(Xk[3] - Xk[0]) * ids, (Xk[4] - Xk[1]) * ids, (Xk[5] - Xk[2]) * ids};
     const double s_mid = ((double)ni.x + 0.5) * ds;
     const double om2 = -L.p.wave_k * L.p.wave_k * L.p.wave_A * sin(L.p.wave_k * s_mid + L.p.wave_f * t);
     double F[3] = {0, 0, 0}, Nm[3] = {0, 0, 0};
@@ -131,8 +132,8 @@ __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__
     for (int i = 0; i < 3; ++i) {
         const double Fi = L.p.b[i] * (dot3(e, Dh + 3 * i) - (i == 2 ? 1.0 : 0.0));
         const int j = (i + 1) % 3, l = (i + 2) % 3;
-        const double dD[3] = {(Dk1[3 * j] - Dk[3 * j]) / ds, (Dk1[3 * j + 1] - Dk[3 * j + 1]) / ds,
-                              (Dk1[3 * j + 2] - Dk[3 * j + 2]) / ds};
+        const double dD[3] = {(Dk1[3 * j] - Dk[3 * j]) * ids, (Dk1[3 * j + 1] - Dk[3 * j + 1]) * ids,
+                              (Dk1[3 * j + 2] - Dk[3 * j + 2]) * ids};
         const double Ni = L.p.a[i] * (dot3(dD, Dh + 3 * l) - (i == 1 ? om2 : 0.0));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -195,29 +196,46 @@ __global__ void rod_node_kernel(const RodLaunch L, const double* __restrict__ X,
     }
 }
 
-// Eq. (newD): rotate the three directors of node k by |w| h about w / |w| (unchanged if w = 0).
+// Eq. (newD): rotate the three directors of node k by |w| h about w / |w| (unchanged if w = 0),
+// written without normalising w: with theta^2 = |w|^2 h^2,
+//   D' = cos(theta) D + (sin(theta)/theta) h (w x D) + ((1 - cos(theta))/theta^2) h^2 (w.D) w,
+// the two ratios taken from their Taylor series in theta^2 when theta^2 < 1e-3 (the next terms
+// are below 1e-22, i.e. exact in float64) and from sincos otherwise.  Small angles -- the usual
+// case, |w| dt ~ 1e-4..1e-3 -- then need no sqrt, division or trigonometric call, which matters
+// because the float64 pipe bounds this kernel.
 __device__ __forceinline__ void rodrigues(const double* D0, double wx, double wy, double wz,
                                           double h, double* D1)
 {
-    const double wn = sqrt(wx * wx + wy * wy + wz * wz);
-    if (wn == 0.0) {
+    const double w2 = wx * wx + wy * wy + wz * wz;
+    if (w2 == 0.0) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) D1[q] = D0[q];
         return;
     }
-    const double e[3] = {wx / wn, wy / wn, wz / wn};
-    double st, ct;
-    sincos(wn * h, &st, &ct);
+    const double q = w2 * h * h;   // theta^2
+    double ct, sc, cc;             // cos(theta), sin(theta)/theta, (1 - cos(theta))/theta^2
+    if (q < 1e-3) {
+        sc = 1.0 + q * (-1.0 / 6.0 + q * (1.0 / 120.0 + q * (-1.0 / 5040.0 + q * (1.0 / 362880.0))));
+        cc = 0.5 + q * (-1.0 / 24.0 + q * (1.0 / 720.0 + q * (-1.0 / 40320.0 + q * (1.0 / 3628800.0))));
+        ct = 1.0 - q * cc;
+    } else {
+        const double th = sqrt(q);
+        double st;
+        sincos(th, &st, &ct);
+        sc = st / th;
+        cc = (1.0 - ct) / q;
+    }
+    const double a = sc * h, b = cc * h * h;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const double* v = D0 + 3 * i;
-        const double ev = e[0] * v[0] + e[1] * v[1] + e[2] * v[2];
-        const double c0 = e[1] * v[2] - e[2] * v[1];
-        const double c1 = e[2] * v[0] - e[0] * v[2];
-        const double c2 = e[0] * v[1] - e[1] * v[0];
-        D1[3 * i + 0] = ct * v[0] + st * c0 + (1.0 - ct) * ev * e[0];
-        D1[3 * i + 1] = ct * v[1] + st * c1 + (1.0 - ct) * ev * e[1];
-        D1[3 * i + 2] = ct * v[2] + st * c2 + (1.0 - ct) * ev * e[2];
+        const double wv = b * (wx * v[0] + wy * v[1] + wz * v[2]);
+        const double c0 = wy * v[2] - wz * v[1];
+        const double c1 = wz * v[0] - wx * v[2];
+        const double c2 = wx * v[1] - wy * v[0];
+        D1[3 * i + 0] = ct * v[0] + a * c0 + wv * wx;
+        D1[3 * i + 1] = ct * v[1] + a * c1 + wv * wy;
+        D1[3 * i + 2] = ct * v[2] + a * c2 + wv * wz;
     }
 }
 

@@ -31,6 +31,7 @@ EXPORTS = [
     "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run", "mrs_velocity_noalloc",
     "serve_create", "serve_submit", "serve_poll", "serve_drain", "serve_stats", "serve_destroy",
     "mrs_autotune", "mrs_autotune_save", "mrs_autotune_load", "parareal_run_pipelined",
+    "rod_advance", "rod_checkpoint_save", "rod_checkpoint_load",
 ]
 MRS_JOB_VELOCITY, MRS_JOB_ROD = 0, 1
 
@@ -117,6 +118,11 @@ def lib():
                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, _vp]
         L.rot_sqrt_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+        L.rod_checkpoint_save.argtypes = [ctypes.c_char_p, ctypes.c_int, _i64p, _vp, _vp,
+                                          ctypes.c_double, _vp]
+        L.rod_checkpoint_load.argtypes = [ctypes.c_char_p, ctypes.c_int, _i64p, _vp, _vp, _dp, _vp]
+        L.rod_advance.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.c_double,
+                                  ctypes.c_int, _vp]
         L.parareal_run_pipelined.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.POINTER(RodParams),
                                              _vp, _vp, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -295,6 +301,30 @@ def rod_step(ctx: Context, rod_off, params: RodParams, X, D, t0, dt, nsteps, sch
     _check(lib().rod_step(ctx.handle, len(off) - 1, poff, ctypes.byref(params), _ptr(X), _ptr(D),
                           float(t0), float(dt), int(nsteps), int(scheme), int(precision),
                           _stream(stream)))
+
+
+def rod_advance(ctx: Context, X, D, u, w, dt, stream=None):
+    """``rod_advance``: X += u dt, frames rotated by |w| dt about w (in place, device float64
+    state; u, w float32 or float64 tensors)."""
+    import torch
+    _check(lib().rod_advance(ctx.handle, int(X.shape[0]), _ptr(X), _ptr(D), _ptr(u), _ptr(w),
+                             float(dt), 1 if u.dtype == torch.float64 else 0, _stream(stream)))
+
+
+def rod_checkpoint_save(path, rod_off, X, D, t, stream=None):
+    """``rod_checkpoint_save``: write t, offsets, X, D (device float64 tensors) to a file."""
+    off, poff = _offsets(rod_off)
+    _check(lib().rod_checkpoint_save(path.encode(), len(off) - 1, poff, _ptr(X), _ptr(D), float(t),
+                                     _stream(stream)))
+
+
+def rod_checkpoint_load(path, rod_off, X, D, stream=None):
+    """``rod_checkpoint_load``: fill X, D from a checkpoint file; returns its time t."""
+    off, poff = _offsets(rod_off)
+    t = ctypes.c_double()
+    _check(lib().rod_checkpoint_load(path.encode(), len(off) - 1, poff, _ptr(X), _ptr(D),
+                                     ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 def rot_sqrt_batch(ctx: Context, R, S, stream=None):

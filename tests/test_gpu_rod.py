@@ -237,3 +237,73 @@ def test_rod_forces_with_lj_match_oracle(ctx, orc):
     ref = go + lj
     assert np.abs(g.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
     assert np.abs(m.cpu().numpy() - mo).max() <= 1e-11 * np.abs(mo).max()
+
+
+def test_rod_advance_matches_oracle(ctx, orc):
+    """Eqs. newx/newD with given velocities, float32 and float64 velocity inputs."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(76, 3, 50)
+    rng = np.random.default_rng(76)
+    u = rng.standard_normal(rs.X.shape)
+    w = rng.standard_normal(rs.X.shape) * 30.0
+    w[5] = 0.0
+    dt = 1e-3
+    for dtype in (torch.float32, torch.float64):
+        uu = torch.from_numpy(u).to(dtype).cuda()
+        ww = torch.from_numpy(w).to(dtype).cuda()
+        Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+        mrs.rod_advance(ctx, Xd, Dd, uu, ww, dt)
+        torch.cuda.synchronize()
+        ug = uu.double().cpu().numpy()
+        wg = ww.double().cpu().numpy()
+        np.testing.assert_allclose(Xd.cpu().numpy(), rs.X + ug * dt, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(Dd.cpu().numpy(), orc.rodrigues_update(rs.D, wg, dt), rtol=0, atol=1e-14)
+
+
+def test_checkpoint_resume_is_exact(ctx, tmp_path):
+    """Stepping 30 steps, or 12 steps + checkpoint + restore into fresh buffers + 18 steps, gives
+    bit-identical states; corrupted or mismatched checkpoints are rejected."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(77, 2, 48, box=2.0)
+    cfg = dict(W.ROD_PLAIN)
+    gp, _ = params(cfg, rs.eps)
+    dt = 1e-6
+    Xa, Da = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+    mrs.rod_step(ctx, rs.rod_off, gp, Xa, Da, 0.0, dt, 30, mrs.MRS_RK2)
+    Xb, Db = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+    mrs.rod_step(ctx, rs.rod_off, gp, Xb, Db, 0.0, dt, 12, mrs.MRS_RK2)
+    path = str(tmp_path / "rods.ckpt")
+    mrs.rod_checkpoint_save(path, rs.rod_off, Xb, Db, 12 * dt)
+    Xc, Dc = torch.zeros_like(Xb), torch.zeros_like(Db)
+    t = mrs.rod_checkpoint_load(path, rs.rod_off, Xc, Dc)
+    assert t == 12 * dt
+    mrs.rod_step(ctx, rs.rod_off, gp, Xc, Dc, t, dt, 18, mrs.MRS_RK2)
+    torch.cuda.synchronize()
+    assert torch.equal(Xa, Xc) and torch.equal(Da, Dc)
+    raw = bytearray(open(path, "rb").read())
+    raw[100] ^= 0xFF
+    bad = str(tmp_path / "bad.ckpt")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(mrs.MrsError):
+        mrs.rod_checkpoint_load(bad, rs.rod_off, Xc, Dc)
+    with pytest.raises(mrs.MrsError):
+        mrs.rod_checkpoint_load(path, [0, 48], Xc[:48], Dc[:48])
+
+
+def test_parareal_reports_non_convergence(ctx):
+    """Too few iterations for the tolerance, and an unstable coarse step, both give MRS_ENOCONV
+    (the state then holds the last iterate)."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(78, 2, 24, box=1.5)
+    cfg = dict(W.WAVE, a=(2e-3,) * 3, b=(0.3,) * 3)
+    gp, _ = params(cfg, rs.eps)
+    Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+    with pytest.raises(mrs.MrsError) as e:
+        mrs.parareal_run(ctx, rs.rod_off, gp, Xd, Dd, 0.0, 8 * 16 * 5e-5, 8, 5e-5, 4, 1, 1e-30)
+    assert e.value.status == mrs.MRS_ENOCONV
+    stiff = dict(W.WAVE, a=(5.0,) * 3, b=(500.0,) * 3)
+    gs, _ = params(stiff, rs.eps)
+    Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+    st = mrs.parareal_run(ctx, rs.rod_off, gs, Xd, Dd, 0.0, 4 * 64 * 1e-4, 4, 1e-4, 64, 4, 1e-10,
+                          raise_on_noconv=False)
+    assert not (st.final_incr < 1e-10)
