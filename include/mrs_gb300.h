@@ -50,6 +50,7 @@ extern "C" {
 #define MRS_ENOCONV   5   /* Parareal did not reach the tolerance, or its increment diverged */
 #define MRS_EBUSY     6   /* serving: no free slot / budget for the job right now */
 #define MRS_PENDING   7   /* serving: the job has not finished yet */
+#define MRS_ECANCELED 8   /* serving: the job was cancelled before it was admitted */
 
 /* ---- arithmetic of the pair sum ---------------------------------------------------------- */
 #define MRS_F64       0   /* float64 inputs/outputs, float64 arithmetic */
@@ -80,6 +81,12 @@ MRS_API int mrs_ctx_destroy(mrs_ctx* ctx);
 
 /* Number of SMs of the context's device (host-side query; no GPU work). */
 MRS_API int mrs_ctx_num_sms(const mrs_ctx* ctx);
+
+/* Device-side anomaly flags raised by the pair-sum kernels of this context since the last call
+ * (MRS_FLAG_NONFINITE: a non-finite u or omega was written, e.g. from non-finite inputs).
+ * Synchronizes the device, returns the flags in *flags and clears them. */
+#define MRS_FLAG_NONFINITE 1u
+MRS_API int mrs_device_status(mrs_ctx* ctx, unsigned int* flags);
 
 /* ==========================================================================================
  * MRS pair sum -- Section II-C, Eqs. (velocity_field), (angular_velocity_field),
@@ -330,6 +337,11 @@ MRS_API int serve_submit(mrs_server* srv, const mrs_job* job, uint64_t* ticket);
  * has finished and its results are in the caller's buffers; returns MRS_PENDING (done = 0)
  * while it is queued or running, MRS_OK when done, or the job's error status. */
 MRS_API int serve_poll(mrs_server* srv, uint64_t ticket, int* done, double* latency_s);
+
+/* Cancel a job that has not been admitted yet: it finishes with status MRS_ECANCELED and its
+ * buffers are never touched.  Errors: MRS_EBUSY (already admitted, it will run to completion),
+ * MRS_EINVAL (unknown or finished ticket). */
+MRS_API int serve_cancel(mrs_server* srv, uint64_t ticket);
 
 /* Block until every submitted job has finished (or timeout_s seconds pass: MRS_ETIMEOUT). */
 MRS_API int serve_drain(mrs_server* srv, double timeout_s);

@@ -242,6 +242,7 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
         L.Xt = (const double*)ins[3];
         L.u = (double*)u;
         L.w = (double*)w;
+        L.err = p->ctx->d_err;
         e = launch_mrs_f64(L, s);
     } else {
         if (p->n_tiles == 0) return MRS_OK;
@@ -259,6 +260,7 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
         L.w = (float*)w;
         L.partial = p->d_partial;
         L.counters = p->d_counters;
+        L.err = p->ctx->d_err;
         e = launch_mrs_f32(p->config, p->precision == MRS_F32_COMP, L, s);
     }
     if (e != cudaSuccess) {
@@ -294,6 +296,13 @@ int mrs_ctx_create(mrs_ctx** ctx, int device)
                 prop.major, prop.minor);
     mrs_ctx* c = new mrs_ctx();
     c->device = device;
+    if (cudaMalloc((void**)&c->d_err, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(unsigned int)) != cudaSuccess) {
+        cudaFree(c->d_err);
+        delete c;
+        set_error("device error word allocation failed");
+        return MRS_ENOMEM;
+    }
     c->num_sms = prop.multiProcessorCount;
     c->cc_major = prop.major;
     c->cc_minor = prop.minor;
@@ -312,11 +321,23 @@ int mrs_ctx_destroy(mrs_ctx* ctx)
     ctx->plan_cache.clear();
     for (RodWorkspace* w : ctx->rod_ws) rod_ws_free(w);
     ctx->rod_ws.clear();
+    cudaFree(ctx->d_err);
     delete ctx;
     return MRS_OK;
 }
 
 int mrs_ctx_num_sms(const mrs_ctx* ctx) { return ctx ? ctx->num_sms : 0; }
+
+int mrs_device_status(mrs_ctx* ctx, unsigned int* flags)
+{
+    clear_error();
+    MRS_REQUIRE(ctx != nullptr && flags != nullptr, "NULL argument");
+    MRS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    MRS_CHECK_CUDA(cudaDeviceSynchronize());
+    MRS_CHECK_CUDA(cudaMemcpy(flags, ctx->d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost));
+    MRS_CHECK_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+    return MRS_OK;
+}
 
 int mrs_plan_create(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
                     const double* eps_per_sys, int precision, int config, mrs_plan** plan)

@@ -91,6 +91,7 @@ struct MrsLaunch {
     float* w;
     float* partial;       // [2P][12][TM] floats
     int* counters;        // [n_tiles], zero between launches
+    unsigned int* err;    // device error word: bit 0 = a non-finite output was written
 };
 
 cudaError_t launch_mrs_f32(int config, bool comp, const MrsLaunch& L, cudaStream_t s);
@@ -110,6 +111,7 @@ struct MrsLaunch64 {
     const double* Xt;
     double* u;
     double* w;
+    unsigned int* err;
 };
 cudaError_t launch_mrs_f64(const MrsLaunch64& L, cudaStream_t s);
 constexpr int kF64Block = 128;
@@ -168,6 +170,7 @@ struct mrs_plan {
 
 struct mrs_ctx {
     int device = 0;
+    unsigned int* d_err = nullptr;   // device error word (see mrs_device_status)
     int num_sms = 0;
     int cc_major = 0, cc_minor = 0;
     size_t smem_per_block_optin = 0;

@@ -365,6 +365,7 @@ mrs_f32_persistent(const MrsLaunch L)
                             v = acc[k][q];
                         }
                         v *= sc.scale;
+                        if (!isfinite(v)) atomicOr(L.err, 1u);
                         if (q < 3) L.u[gi * 3 + q] = v; else L.w[gi * 3 + q - 3] = v;
                     }
                 }
@@ -438,6 +439,7 @@ mrs_f32_persistent(const MrsLaunch L)
 #pragma unroll
                         for (int q = 0; q < 6; ++q) {
                             const float val = __fsub_rn(tot[q], cmp[q]) * sc.scale;
+                            if (!isfinite(val)) atomicOr(L.err, 1u);
                             if (q < 3) L.u[gi * 3 + q] = val; else L.w[gi * 3 + q - 3] = val;
                         }
                     }
@@ -562,6 +564,7 @@ __global__ void __launch_bounds__(kF64Block) mrs_f64_kernel(const MrsLaunch64 L)
     }
     if (valid) {
         const double sc = L.inv_mu / (8.0 * 3.14159265358979323846);
+        if (!isfinite(u0 + u1 + u2 + w0 + w1 + w2)) atomicOr(L.err, 1u);
         L.u[i * 3 + 0] = u0 * sc;
         L.u[i * 3 + 1] = u1 * sc;
         L.u[i * 3 + 2] = u2 * sc;

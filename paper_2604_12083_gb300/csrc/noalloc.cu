@@ -34,7 +34,8 @@ constexpr size_t kNaCountersBytes = (size_t)kNaMaxTiles * sizeof(int);
 constexpr size_t kNaOffTiles = 0;
 constexpr size_t kNaOffCounters = kNaOffTiles + kNaTilesBytes;
 constexpr size_t kNaOffConst = kNaOffCounters + kNaCountersBytes;
-constexpr size_t kNaOffPartial = (kNaOffConst + sizeof(SysConst) + 255) / 256 * 256;
+constexpr size_t kNaOffErr = kNaOffConst + sizeof(SysConst);
+constexpr size_t kNaOffPartial = (kNaOffErr + sizeof(unsigned int) + 255) / 256 * 256;
 constexpr size_t kNaScratchBytes = kNaOffPartial + kNaPartialBytes;   // ~18.3 MiB
 
 }  // namespace
@@ -160,6 +161,7 @@ extern "C" int mrs_velocity_noalloc(int64_t n_points, const float* X, const floa
     L.w = w;
     L.partial = partial;
     L.counters = counters;
+    L.err = (unsigned int*)(base + kNaOffErr);   // a word of the array nobody reads back
     cudaError_t e = launch_mrs_f32(kNaConfig, true, L, s);
     if (e != cudaSuccess) {
         set_error("pair-sum launch failed: %s", cudaGetErrorString(e));

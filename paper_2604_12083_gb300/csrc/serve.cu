@@ -173,6 +173,7 @@ struct mrs_server {
     int peak_active = 0;
     bool stop = false;
     int fatal = MRS_OK;
+    char fatal_msg[512] = "";
     std::thread th;
     struct Iter {
         cudaEvent_t end;
@@ -189,7 +190,8 @@ void fail_all(mrs_server* S, int status, const char* what, cudaError_t e)
 {
     std::lock_guard<std::mutex> g(S->mu);
     S->fatal = status;
-    set_error("serving: %s failed: %s", what, cudaGetErrorString(e));
+    snprintf(S->fatal_msg, sizeof(S->fatal_msg), "serving: %s failed: %s", what, cudaGetErrorString(e));
+    set_error("%s", S->fatal_msg);
     for (auto& kv : S->jobs) {
         SJob* j = kv.second;
         if (!j->finished) {
@@ -345,6 +347,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
     L.w = S->pw;
     L.partial = S->d_partial;
     L.counters = S->d_counters;
+    L.err = S->ctx->d_err;
     if ((e = launch_mrs_f32(S->config, true, L, s))) return e;
     // stage updates and copy-out
     std::vector<SJob*> keep;
@@ -615,7 +618,36 @@ int serve_poll(mrs_server* S, uint64_t ticket, int* done, double* latency_s)
     if (done) *done = j->finished ? 1 : 0;
     if (!j->finished) return MRS_PENDING;
     if (latency_s) *latency_s = j->t_done - j->t_submit;
+    if (j->status == MRS_ECANCELED) set_error("job %llu was cancelled", (unsigned long long)ticket);
+    else if (j->status != MRS_OK) set_error("%s", S->fatal_msg);
     return j->status;
+}
+
+int serve_cancel(mrs_server* S, uint64_t ticket)
+{
+    clear_error();
+    MRS_REQUIRE(S != nullptr, "NULL server");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->jobs.find(ticket);
+    MRS_REQUIRE(it != S->jobs.end(), "unknown ticket %llu", (unsigned long long)ticket);
+    SJob* j = it->second;
+    for (auto w = S->waiting.begin(); w != S->waiting.end(); ++w) {
+        if (*w == j) {
+            S->waiting.erase(w);
+            j->finished = true;
+            j->status = MRS_ECANCELED;
+            j->t_done = now_s();
+            S->completed += 1;
+            S->cv_done.notify_all();
+            return MRS_OK;
+        }
+    }
+    if (j->finished) {
+        set_error("job %llu has already finished", (unsigned long long)ticket);
+        return MRS_EINVAL;
+    }
+    set_error("job %llu is already running and cannot be cancelled", (unsigned long long)ticket);
+    return MRS_EBUSY;
 }
 
 int serve_drain(mrs_server* S, double timeout_s)

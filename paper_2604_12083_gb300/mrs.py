@@ -18,10 +18,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libmrs_gb300.so")
 
 MRS_OK, MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA, MRS_ETIMEOUT, MRS_ENOCONV, MRS_EBUSY, MRS_PENDING = range(8)
+MRS_ECANCELED = 8
 MRS_F64, MRS_F32, MRS_F32_COMP = 0, 1, 2
 MRS_EULER, MRS_RK2 = 0, 1
 STATUS_NAMES = {0: "MRS_OK", 1: "MRS_EINVAL", 2: "MRS_ENOMEM", 3: "MRS_ECUDA", 4: "MRS_ETIMEOUT",
-                5: "MRS_ENOCONV", 6: "MRS_EBUSY", 7: "MRS_PENDING"}
+                5: "MRS_ENOCONV", 6: "MRS_EBUSY", 7: "MRS_PENDING", 8: "MRS_ECANCELED"}
 
 # Every symbol include/mrs_gb300.h declares (kept in sync by tests/test_abi.py).
 EXPORTS = [
@@ -30,9 +31,11 @@ EXPORTS = [
     "mrs_plan_config_count", "mrs_plan_config_info", "mrs_plan_info",
     "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run", "mrs_velocity_noalloc",
     "serve_create", "serve_submit", "serve_poll", "serve_drain", "serve_stats", "serve_destroy",
+    "serve_cancel",
     "mrs_autotune", "mrs_autotune_save", "mrs_autotune_load", "parareal_run_pipelined",
-    "rod_advance", "rod_checkpoint_save", "rod_checkpoint_load",
+    "rod_advance", "rod_checkpoint_save", "rod_checkpoint_load", "mrs_device_status",
 ]
+MRS_FLAG_NONFINITE = 1
 MRS_JOB_VELOCITY, MRS_JOB_ROD = 0, 1
 
 _vp = ctypes.c_void_p
@@ -104,6 +107,7 @@ def lib():
         L.mrs_ctx_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
         L.mrs_ctx_destroy.argtypes = [_vp]
         L.mrs_ctx_num_sms.argtypes = [_vp]
+        L.mrs_device_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint)]
         L.mrs_velocity.argtypes = [_vp, ctypes.c_int, _i64p, _vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _vp]
         L.mrs_plan_create.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_double, ctypes.c_double,
@@ -136,6 +140,7 @@ def lib():
         L.serve_submit.argtypes = [_vp, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]
         L.serve_poll.argtypes = [_vp, ctypes.c_uint64, _ip, _dp]
         L.serve_drain.argtypes = [_vp, ctypes.c_double]
+        L.serve_cancel.argtypes = [_vp, ctypes.c_uint64]
         L.serve_stats.argtypes = [_vp, _i64p, _i64p, _dp, _ip, ctypes.POINTER(ctypes.c_size_t)]
         L.serve_destroy.argtypes = [_vp]
         L.mrs_velocity_noalloc.argtypes = [ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
@@ -184,6 +189,12 @@ class Context:
     @property
     def num_sms(self) -> int:
         return int(lib().mrs_ctx_num_sms(self.handle))
+
+    def device_status(self) -> int:
+        """``mrs_device_status``: anomaly flags since the last call (synchronizes, clears)."""
+        f = ctypes.c_uint()
+        _check(lib().mrs_device_status(self.handle, ctypes.byref(f)))
+        return f.value
 
     def close(self):
         if self.handle:
@@ -395,6 +406,10 @@ class Server:
         _check(st)
         self._keep.pop(ticket, None)
         return True, lat.value
+
+    def cancel(self, ticket):
+        """``serve_cancel``: cancel a job that has not been admitted yet."""
+        _check(lib().serve_cancel(self.handle, ctypes.c_uint64(ticket)))
 
     def drain(self, timeout_s=600.0):
         _check(lib().serve_drain(self.handle, float(timeout_s)))

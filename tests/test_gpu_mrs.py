@@ -232,3 +232,20 @@ def test_config_table_size(ctx):
     for c in range(15):
         info = mrs.plan_config_info(ctx, c)
         assert info["ctas_per_sm"] >= 1
+
+
+def test_nonfinite_inputs_raise_the_device_flag(ctx):
+    """A NaN force makes non-finite velocities; the context's device flag reports it once."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.single_system(seed=67, n_fil=2, M=600)
+    assert ctx.device_status() == 0
+    for prec in (mrs.MRS_F32_COMP, mrs.MRS_F64):
+        dt = torch.float64 if prec == mrs.MRS_F64 else torch.float32
+        X, f, n = (torch.from_numpy(a).to(dt).cuda() for a in (p.X, p.f, p.n))
+        u, w = torch.empty_like(X), torch.empty_like(X)
+        mrs.mrs_velocity(ctx, p.offsets, X, f, n, u, w, p.mu, float(p.eps[0]), precision=prec)
+        assert ctx.device_status() == 0
+        f[17, 1] = float("nan")
+        mrs.mrs_velocity(ctx, p.offsets, X, f, n, u, w, p.mu, float(p.eps[0]), precision=prec)
+        assert ctx.device_status() & mrs.MRS_FLAG_NONFINITE
+        assert ctx.device_status() == 0

@@ -141,3 +141,25 @@ def test_invalid_and_oversize_jobs(ctx):
         assert e.value.status == mrs.MRS_EINVAL
     finally:
         srv.close()
+
+
+def test_cancel_waiting_job(ctx):
+    """With one slot, a second job waits behind a long rod job and can be cancelled; a running
+    job cannot; the cancelled job's outputs are never written."""
+    from paper_2604_12083_gb300 import mrs
+    srv = mrs.Server(ctx, 1 << 28, 1)
+    try:
+        t_long, _ = run_rod(srv, rod_job(500, 4, M=256), nsteps=1500, scheme=0)
+        t_wait, bw = run_velocity(srv, velocity_job(501, 4))
+        srv.cancel(t_wait)
+        with pytest.raises(mrs.MrsError) as e:
+            srv.cancel(t_long)
+        assert e.value.status in (mrs.MRS_EBUSY, mrs.MRS_EINVAL)
+        srv.drain()
+        with pytest.raises(mrs.MrsError) as e:
+            srv.poll(t_wait)
+        assert e.value.status == mrs.MRS_ECANCELED
+        assert torch.isnan(bw[3]).all()          # never written
+        assert srv.poll(t_long)[0]
+    finally:
+        srv.close()
