@@ -71,6 +71,7 @@ struct KernelConfig {
     int tpt;       // targets per thread
     int paired;    // 1: packed f32x2 inner loop (two sources per instruction)
     int unroll;    // source-loop unroll of the packed loop (independent pair chains in flight)
+    int sq;        // 1: s^2 = s*s by a packed multiply instead of an SFU reciprocal
 };
 
 // Configurations compiled into the library (index = plan config id).

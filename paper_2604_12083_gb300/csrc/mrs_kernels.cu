@@ -107,6 +107,7 @@ __device__ __forceinline__ void pair_f32(float xi, float yi, float zi, const flo
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
+template <bool SQ>
 __device__ __forceinline__ void pair_f32x2(const float2 xt, const float2 yt, const float2 zt,  // targets
                                            const float2 X0, const float2 X1, const float2 X2,
                                            const float2 F0, const float2 F1, const float2 F2,
@@ -118,7 +119,8 @@ __device__ __forceinline__ void pair_f32x2(const float2 xt, const float2 yt, con
                  qz = __fadd2_rn(X2, neg2(zt));
     const float2 d = __ffma2_rn(qx, qx, __ffma2_rn(qy, qy, __ffma2_rn(qz, qz, e2)));
     const float2 s = make_float2(sfu_rsqrt(d.x), sfu_rsqrt(d.y));
-    const float2 s2 = make_float2(sfu_rcp(d.x), sfu_rcp(d.y));
+    // SQ: s2 = s s (one packed multiply) instead of a second SFU op per lane
+    const float2 s2 = SQ ? __fmul2_rn(s, s) : make_float2(sfu_rcp(d.x), sfu_rcp(d.y));
     const float2 s3 = __fmul2_rn(s, s2);
     const float2 s5 = __fmul2_rn(s3, s2);
     const float2 h1 = __ffma2_rn(e2, s3, s);
@@ -192,7 +194,7 @@ struct MinBlocks {   // CTAs per SM the register allocation must allow
 // PAIRED: the inner loop runs on packed f32x2 instructions, two sources per instruction
 // (pair_f32x2); sources are then staged structure-of-arrays (nine rows of kChunk floats) so
 // that four consecutive sources of one component are one 16-byte shared load.
-template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL>
+template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL, bool SQ = false>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, TPT>::value))
 mrs_f32_persistent(const MrsLaunch L)
 {
@@ -306,7 +308,7 @@ mrs_f32_persistent(const MrsLaunch L)
                             s9[c] = h == 0 ? make_float2(v[c].x, v[c].y) : make_float2(v[c].z, v[c].w);
 #pragma unroll
                         for (int k = 0; k < TPT; ++k)
-                            pair_f32x2(xn[k][0], xn[k][1], xn[k][2], s9[0], s9[1], s9[2], s9[3],
+                            pair_f32x2<SQ>(xn[k][0], xn[k][1], xn[k][2], s9[0], s9[1], s9[2], s9[3],
                                        s9[4], s9[5], s9[6], s9[7], s9[8], e2, c1, c2, c3, c5,
                                        acc2[k]);
                     }
@@ -460,27 +462,29 @@ const KernelConfig kConfigs[] = {
     {128, 4, 0, 1}, {128, 2, 0, 1}, {128, 8, 0, 1}, {64, 4, 0, 1}, {256, 2, 0, 1}, {128, 1, 0, 1},
     {128, 2, 1, 1}, {128, 4, 1, 1}, {64, 4, 1, 1}, {256, 2, 1, 1},
     {256, 2, 1, 2}, {128, 2, 1, 2}, {128, 1, 1, 1}, {128, 1, 1, 2}, {256, 1, 1, 2},
+    {256, 2, 1, 1, 1}, {256, 1, 1, 2, 1},
 };
 const int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 
-template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL>
+template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL, bool SQ>
 static cudaError_t launch_t(const MrsLaunch& L, cudaStream_t s)
 {
-    mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED, UNROLL><<<L.P, BLOCK, 0, s>>>(L);
+    mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED, UNROLL, SQ><<<L.P, BLOCK, 0, s>>>(L);
     return cudaGetLastError();
 }
 
-template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL>
+template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL, bool SQ>
 static int occ_t(int* n)
 {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        n, mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED, UNROLL>, BLOCK, 0);
+        n, mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED, UNROLL, SQ>, BLOCK, 0);
     return e == cudaSuccess ? MRS_OK : MRS_ECUDA;
 }
 
-#define MRS_CASE(id, B, T, P, U, FN, ...)                                                 \
+#define MRS_CASE_SQ(id, B, T, P, U, Q, FN, ...)                                           \
     case id:                                                                              \
-        return comp ? FN<B, T, true, P, U>(__VA_ARGS__) : FN<B, T, false, P, U>(__VA_ARGS__);
+        return comp ? FN<B, T, true, P, U, Q>(__VA_ARGS__) : FN<B, T, false, P, U, Q>(__VA_ARGS__);
+#define MRS_CASE(id, B, T, P, U, FN, ...) MRS_CASE_SQ(id, B, T, P, U, false, FN, __VA_ARGS__)
 
 #define MRS_DISPATCH(cfg, comp, FN, ...)                                                  \
     switch (cfg) {                                                                        \
@@ -499,6 +503,8 @@ static int occ_t(int* n)
         MRS_CASE(12, 128, 1, true, 1, FN, __VA_ARGS__)                                    \
         MRS_CASE(13, 128, 1, true, 2, FN, __VA_ARGS__)                                    \
         MRS_CASE(14, 256, 1, true, 2, FN, __VA_ARGS__)                                    \
+        MRS_CASE_SQ(15, 256, 2, true, 1, true, FN, __VA_ARGS__)                           \
+        MRS_CASE_SQ(16, 256, 1, true, 2, true, FN, __VA_ARGS__)                           \
     default: break;                                                                       \
     }
 

@@ -98,7 +98,7 @@ def ragged_batch():
     return W.MRSProblem("ragged", off, f32(Xs), f32(fs), f32(ns), eps, 1.3)
 
 
-@pytest.mark.parametrize("config", list(range(15)))
+@pytest.mark.parametrize("config", list(range(17)))
 @pytest.mark.parametrize("precision", [1, 2])
 def test_ragged_batch_every_config(ctx, orc, config, precision):
     p = ragged_batch()
@@ -228,8 +228,8 @@ def test_autotune_picks_a_config_used_by_plans(ctx, orc, tmp_path):
 def test_config_table_size(ctx):
     """Every compiled configuration is covered by the ragged-batch parity test above."""
     from paper_2604_12083_gb300 import mrs
-    assert mrs.plan_config_count() == 15
-    for c in range(15):
+    assert mrs.plan_config_count() == 17
+    for c in range(17):
         info = mrs.plan_config_info(ctx, c)
         assert info["ctas_per_sm"] >= 1
 
