@@ -350,6 +350,7 @@ def extra_parareal(ctx, dev):
             out["runs"].append({
                 "r": r, "schedule": "pipelined (groups of 8)" if gs else "regular",
                 "iterations": st.iterations, "seconds": st.seconds,
+                "converged": bool(st.final_incr < 1e-11),
                 "increments": [st.incr[i] for i in range(st.iterations)],
                 "fine_steps_executed": st.fine_steps,
                 "rel_diff_vs_serial_displacement": float(np.linalg.norm(disp_p - disp_s) /
@@ -357,7 +358,7 @@ def extra_parareal(ctx, dev):
     # a small, launch-bound system: one 128-node rod, where batching the 64 slices of each
     # iteration into one launch per stage uses the GPU far better than serial stepping
     rs1 = W.rod_system(1, 1, 128)
-    c1 = W.ROD_PLAIN
+    c1 = W.ROD_PARAREAL_128
     prm1 = mrs.RodParams.make(c1["L"], c1["a"], c1["b"], c1["wave_A"], c1["wave_k"], c1["wave_f"],
                               1.0, rs1.eps)
     nf1 = 256
@@ -380,9 +381,11 @@ def extra_parareal(ctx, dev):
                                   raise_on_noconv=False, group_size=gs)
         dp = Xp.cpu().numpy() - rs1.X
         ds_ = Xs.cpu().numpy() - rs1.X
+        ok = bool(st.final_incr < 1e-11)
         small["runs"].append({"schedule": "pipelined (groups of 8)" if gs else "regular",
                               "iterations": st.iterations, "seconds": st.seconds,
-                              "speedup_vs_serial_fine": t_serial1 / st.seconds,
+                              "converged": ok, "final_increment": st.final_incr,
+                              "speedup_vs_serial_fine": t_serial1 / st.seconds if ok else None,
                               "rel_diff_vs_serial_displacement":
                                   float(np.linalg.norm(dp - ds_) / np.linalg.norm(ds_))})
     out["small_system"] = small

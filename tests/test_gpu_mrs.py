@@ -249,3 +249,19 @@ def test_nonfinite_inputs_raise_the_device_flag(ctx):
         mrs.mrs_velocity(ctx, p.offsets, X, f, n, u, w, p.mu, float(p.eps[0]), precision=prec)
         assert ctx.device_status() & mrs.MRS_FLAG_NONFINITE
         assert ctx.device_status() == 0
+
+
+def test_large_ragged_single_system_sampled(ctx, orc):
+    """2^18 + 17 points (6.9e10 pairs, a ragged last tile): 256 sampled targets against all
+    sources, computed one by one by the oracle."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rng = np.random.default_rng(68)
+    N = (1 << 18) + 17
+    X = rng.uniform(0.0, 40.0, (N, 3)).astype(np.float32)
+    f = rng.standard_normal((N, 3)).astype(np.float32)
+    n = rng.standard_normal((N, 3)).astype(np.float32)
+    p = W.MRSProblem("large", np.array([0, N], np.int64), X, f, n, np.array([0.02]), 1.0)
+    u, w = run(ctx, p, mrs.MRS_F32_COMP)
+    idx = np.concatenate([rng.choice(N, 250, replace=False), np.arange(N - 6, N)])
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, 0.02, 1.0, xt=p.X[idx])
+    assert rel_l2(u[idx], ur) < TOL32 and rel_l2(w[idx], wr) < TOL32
