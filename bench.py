@@ -372,16 +372,19 @@ def extra_parareal(ctx, dev):
     mrs.rod_step(ctx, rs1.rod_off, prm1, Xs, Ds, 0.0, dt, Ns * nf1, mrs.MRS_RK2)
     torch.cuda.synchronize()
     t_serial1 = time.perf_counter() - t0
+    # the float32 pair sum puts a floor of ~1e-8 on the relative increment for this system (a
+    # rounding flip of a packed position moves the velocities at the 1e-7 level): tol above it
+    tol1 = 1e-8
     small = {"workload": "one rod, 128 nodes, 64 slices x 256 fine RK2 steps (dt=1e-6), coarse 16 dt",
-             "serial_fine_s": t_serial1, "runs": []}
+             "tol": tol1, "serial_fine_s": t_serial1, "runs": []}
     for gs in (0, 8):
         for rep in range(2):
             Xp, Dp = fresh1()
-            st = mrs.parareal_run(ctx, rs1.rod_off, prm1, Xp, Dp, 0.0, T1s, Ns, dt, 16, 8, 1e-11,
+            st = mrs.parareal_run(ctx, rs1.rod_off, prm1, Xp, Dp, 0.0, T1s, Ns, dt, 16, 8, tol1,
                                   raise_on_noconv=False, group_size=gs)
         dp = Xp.cpu().numpy() - rs1.X
         ds_ = Xs.cpu().numpy() - rs1.X
-        ok = bool(st.final_incr < 1e-11)
+        ok = bool(st.final_incr < tol1)
         small["runs"].append({"schedule": "pipelined (groups of 8)" if gs else "regular",
                               "iterations": st.iterations, "seconds": st.seconds,
                               "converged": ok, "final_increment": st.final_incr,

@@ -17,6 +17,9 @@
  *    D[k*9 + i*3 + c]: component c of director D^{i+1} of node k (rows are directors).
  *  - Independent systems (or rods) are concatenated along the point axis and delimited by
  *    CSR offsets: offsets[0] = 0 <= offsets[1] <= ... <= offsets[n] = total points.
+ *  - A context (and everything created from it) is used by one host thread at a time; its plan
+ *    and workspace caches are not locked.  A server (serve_*) may be driven from any thread:
+ *    its scheduler runs on a thread and stream of its own.
  *  - Work is enqueued on the caller's CUDA stream (`stream`, a cudaStream_t passed as void*;
  *    NULL = the legacy default stream) and the call returns without synchronizing, except
  *    where an entry point says otherwise.

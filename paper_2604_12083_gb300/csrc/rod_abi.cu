@@ -53,7 +53,7 @@ void rod_ws_free(RodWorkspace* ws)
     for (auto& g : ws->graphs) cudaGraphExecDestroy(g.exec);
     if (ws->cap) cudaStreamDestroy(ws->cap);
     if (ws->plan) plan_free(ws->plan);
-    void* ptrs[] = {ws->d_node_info, ws->d_t0, ws->d_step, ws->d_FN, ws->d_Xf, ws->d_gf, ws->d_mf,
+    void* ptrs[] = {ws->d_node_info, ws->d_chunks, ws->d_t0, ws->d_step, ws->d_FN, ws->d_Xf, ws->d_gf, ws->d_mf,
                     ws->d_u, ws->d_w, ws->d_g64, ws->d_m64, ws->d_u64, ws->d_w64, ws->d_Xh, ws->d_Dh};
     for (void* q : ptrs) cudaFree(q);
     delete ws;
@@ -87,13 +87,18 @@ int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int
     ws->N = ws->N1 * n_inst;
     const size_t N = (size_t)ws->N;
     std::vector<int2> info(N);
+    std::vector<int> chunks;
     for (int i = 0; i < n_inst; ++i)
         for (int r = 0; r < n_rods; ++r) {
             const int M = (int)(rod_off[r + 1] - rod_off[r]);
             for (int k = 0; k < M; ++k) info[(size_t)i * ws->N1 + rod_off[r] + k] = make_int2(k, M);
+            for (int c = 0; c < M; c += kRodChunk - 1)
+                chunks.push_back((int)((size_t)i * ws->N1 + rod_off[r] + c));
         }
+    ws->n_chunks = (int)chunks.size();
     int st;
-    if ((st = dalloc(&ws->d_node_info, N)) || (st = dalloc(&ws->d_t0, n_inst)) ||
+    if ((st = dalloc(&ws->d_node_info, N)) || (st = dalloc(&ws->d_chunks, chunks.size())) ||
+        (st = dalloc(&ws->d_t0, n_inst)) ||
         (st = dalloc(&ws->d_step, 1)) || (st = dalloc(&ws->d_FN, 6 * N)) ||
         (st = dalloc(&ws->d_Xh, 3 * N)) || (st = dalloc(&ws->d_Dh, 9 * N))) {
         rod_ws_free(ws);
@@ -114,6 +119,7 @@ int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int
         }
     }
     cudaMemcpy(ws->d_node_info, info.data(), N * sizeof(int2), cudaMemcpyHostToDevice);
+    cudaMemcpy(ws->d_chunks, chunks.data(), chunks.size() * sizeof(int), cudaMemcpyHostToDevice);
     cudaMemset(ws->d_t0, 0, n_inst * sizeof(double));
     cudaMemset(ws->d_step, 0, sizeof(long long));
     if (eps > 0.0) {
@@ -154,6 +160,8 @@ RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt)
     L.dt = dt;
     L.p = *p;
     L.FN = ws->d_FN;
+    L.chunks = ws->d_chunks;
+    L.n_chunks = ws->n_chunks;
     return L;
 }
 

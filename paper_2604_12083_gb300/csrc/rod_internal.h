@@ -13,8 +13,11 @@ struct RodLaunch {
     long long* step;           // step counter of the current run (time = t0 + step * dt)
     double dt;
     mrs_rod_params p;
-    double* FN;                // [N][6] segment force / moment scratch
+    double* FN;                // [N][6] segment force / moment scratch (two-kernel path)
+    const int* chunks;         // [n_chunks] base node of every fused-kernel chunk, or NULL
+    int n_chunks;
 };
+constexpr int kRodChunk = 128;   // threads per fused rod-force CTA (kRodChunk - 1 nodes each)
 
 cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double* D, double t_off,
                               double* g64, double* m64, float* Xf, float* gf, float* mf,
@@ -41,6 +44,8 @@ struct RodWorkspace {
     int precision = MRS_F32_COMP;
     std::vector<int64_t> rod_off;   // per instance, n_rods+1
     int2* d_node_info = nullptr;
+    int* d_chunks = nullptr;
+    int n_chunks = 0;
     double* d_t0 = nullptr;
     long long* d_step = nullptr;
     double* d_FN = nullptr;

@@ -96,17 +96,15 @@ __global__ void rot_sqrt_batch_kernel(int n, const double* R, double* S)
     if (i < n) rot_sqrt_dev(R + 9 * (size_t)i, S + 9 * (size_t)i);
 }
 
-// Segment k+1/2: internal force F and moment N in lab coordinates (Eqs. mid_triad,
-// F_comp_discrete, N_comp_discrete; Omega of Section IV-A at the segment midpoint).
-__global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__ X,
-                                   const double* __restrict__ D, double t_off)
+// Segment k+1/2 (index idx within a rod of M nodes): internal force F and moment N in lab
+// coordinates (Eqs. mid_triad, F_comp_discrete, N_comp_discrete; Omega of Section IV-A at the
+// segment midpoint), written to o[0..5].
+__device__ void segment_fn(const RodLaunch& L, const double* __restrict__ X,
+                           const double* __restrict__ D, double t_off, long long k, int idx, int M,
+                           double* o)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L.N) return;
-    const int2 ni = L.node_info[k];
-    if (ni.x >= ni.y - 1) return;  // last node of its rod: no segment
-    const double ds = L.p.L / (double)(ni.y - 1);
-    const int inst = k / L.nodes_per_inst;
+    const double ds = L.p.L / (double)(M - 1);
+    const int inst = (int)(k / L.nodes_per_inst);
     const double t = L.t0[inst] + (double)(*L.step) * L.dt + t_off;
     const double* Dk = D + 9 * (size_t)k;
     const double* Dk1 = Dk + 9;
@@ -125,7 +123,7 @@ __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__
     const double* Xk = X + 3 * (size_t)k;
     const double ids = 1.0 / ds;   // one division; float64 divisions are expensive here
     const double e[3] = {(Xk[3] - Xk[0]) * ids, (Xk[4] - Xk[1]) * ids, (Xk[5] - Xk[2]) * ids};
-    const double s_mid = ((double)ni.x + 0.5) * ds;
+    const double s_mid = ((double)idx + 0.5) * ds;
     const double om2 = -L.p.wave_k * L.p.wave_k * L.p.wave_A * sin(L.p.wave_k * s_mid + L.p.wave_f * t);
     double F[3] = {0, 0, 0}, Nm[3] = {0, 0, 0};
 #pragma unroll
@@ -141,7 +139,6 @@ __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__
             Nm[c] += Ni * Dh[3 * i + c];
         }
     }
-    double* o = L.FN + 6 * (size_t)k;
     o[0] = F[0];
     o[1] = F[1];
     o[2] = F[2];
@@ -150,37 +147,43 @@ __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__
     o[5] = Nm[2];
 }
 
-// Node k: g_k = F_{k+1/2} - F_{k-1/2}, m_k = N_{k+1/2} - N_{k-1/2} + (1/2)(dX_{k+1/2} x F_{k+1/2}
-// + dX_{k-1/2} x F_{k-1/2}) (free ends: missing segments contribute nothing).  Writes the
-// float64 outputs g64/m64 when given, and the float32 copies (X, g, m) the pair sum reads
-// when Xf is given.
-__global__ void rod_node_kernel(const RodLaunch L, const double* __restrict__ X, double* g64,
-                                double* m64, float* Xf, float* gf, float* mf)
+__global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__ X,
+                                   const double* __restrict__ D, double t_off)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.N) return;
     const int2 ni = L.node_info[k];
+    if (ni.x >= ni.y - 1) return;  // last node of its rod: no segment
+    segment_fn(L, X, D, t_off, k, ni.x, ni.y, L.FN + 6 * (size_t)k);
+}
+
+// Node k: g_k = F_{k+1/2} - F_{k-1/2}, m_k = N_{k+1/2} - N_{k-1/2} + (1/2)(dX_{k+1/2} x F_{k+1/2}
+// + dX_{k-1/2} x F_{k-1/2}) (free ends: missing segments contribute nothing; fp / fm point to the
+// segments k+1/2 / k-1/2 or are NULL).  Writes the float64 outputs g64/m64 when given, and the
+// float32 copies (X, g, m) the pair sum reads when Xf is given.
+__device__ __forceinline__ void node_fn(const double* __restrict__ X, long long k, const double* fp,
+                                        const double* fm, double* g64, double* m64, float* Xf,
+                                        float* gf, float* mf)
+{
     const double* Xk = X + 3 * (size_t)k;
     double g[3] = {0, 0, 0}, m[3] = {0, 0, 0};
-    if (ni.x < ni.y - 1) {  // segment k+1/2
-        const double* fn = L.FN + 6 * (size_t)k;
+    if (fp) {  // segment k+1/2
         const double dX[3] = {Xk[3] - Xk[0], Xk[4] - Xk[1], Xk[5] - Xk[2]};
-        g[0] += fn[0];
-        g[1] += fn[1];
-        g[2] += fn[2];
-        m[0] += fn[3] + 0.5 * (dX[1] * fn[2] - dX[2] * fn[1]);
-        m[1] += fn[4] + 0.5 * (dX[2] * fn[0] - dX[0] * fn[2]);
-        m[2] += fn[5] + 0.5 * (dX[0] * fn[1] - dX[1] * fn[0]);
+        g[0] += fp[0];
+        g[1] += fp[1];
+        g[2] += fp[2];
+        m[0] += fp[3] + 0.5 * (dX[1] * fp[2] - dX[2] * fp[1]);
+        m[1] += fp[4] + 0.5 * (dX[2] * fp[0] - dX[0] * fp[2]);
+        m[2] += fp[5] + 0.5 * (dX[0] * fp[1] - dX[1] * fp[0]);
     }
-    if (ni.x > 0) {  // segment k-1/2
-        const double* fn = L.FN + 6 * (size_t)(k - 1);
+    if (fm) {  // segment k-1/2
         const double dX[3] = {Xk[0] - Xk[-3], Xk[1] - Xk[-2], Xk[2] - Xk[-1]};
-        g[0] -= fn[0];
-        g[1] -= fn[1];
-        g[2] -= fn[2];
-        m[0] += -fn[3] + 0.5 * (dX[1] * fn[2] - dX[2] * fn[1]);
-        m[1] += -fn[4] + 0.5 * (dX[2] * fn[0] - dX[0] * fn[2]);
-        m[2] += -fn[5] + 0.5 * (dX[0] * fn[1] - dX[1] * fn[0]);
+        g[0] -= fm[0];
+        g[1] -= fm[1];
+        g[2] -= fm[2];
+        m[0] += -fm[3] + 0.5 * (dX[1] * fm[2] - dX[2] * fm[1]);
+        m[1] += -fm[4] + 0.5 * (dX[2] * fm[0] - dX[0] * fm[2]);
+        m[2] += -fm[5] + 0.5 * (dX[0] * fm[1] - dX[1] * fm[0]);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -194,6 +197,38 @@ __global__ void rod_node_kernel(const RodLaunch L, const double* __restrict__ X,
             mf[3 * (size_t)k + c] = (float)m[c];
         }
     }
+}
+
+__global__ void rod_node_kernel(const RodLaunch L, const double* __restrict__ X, double* g64,
+                                double* m64, float* Xf, float* gf, float* mf)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.N) return;
+    const int2 ni = L.node_info[k];
+    node_fn(X, k, ni.x < ni.y - 1 ? L.FN + 6 * (size_t)k : nullptr,
+            ni.x > 0 ? L.FN + 6 * (size_t)(k - 1) : nullptr, g64, m64, Xf, gf, mf);
+}
+
+// Both steps in one launch.  A CTA covers kRodChunk - 1 consecutive nodes of one rod: thread t
+// computes segment base - 1 + t into shared memory, then threads 1.. emit node base + t - 1,
+// whose two segments are slots t - 1 and t (chunks overlap by one segment, so every thread
+// computes exactly one segment and nothing goes through global memory).  L.chunks[c] is the
+// node index of chunk c's base node.
+__global__ void __launch_bounds__(kRodChunk) rod_forces_fused_kernel(
+    const RodLaunch L, const double* __restrict__ X, const double* __restrict__ D, double t_off,
+    double* g64, double* m64, float* Xf, float* gf, float* mf)
+{
+    __shared__ double sFN[kRodChunk * 6];
+    const long long k0 = L.chunks[blockIdx.x];
+    const int2 ni0 = L.node_info[k0];
+    const int M = ni0.y, t = threadIdx.x;
+    const int s = ni0.x - 1 + t;   // segment index within the rod
+    if (s >= 0 && s < M - 1) segment_fn(L, X, D, t_off, k0 - 1 + t, s, M, sFN + 6 * t);
+    __syncthreads();
+    const int n = ni0.x + t - 1;   // node index within the rod
+    if (t == 0 || n >= M) return;
+    node_fn(X, k0 + t - 1, n < M - 1 ? sFN + 6 * t : nullptr, n > 0 ? sFN + 6 * (t - 1) : nullptr,
+            g64, m64, Xf, gf, mf);
 }
 
 // Eq. (newD): rotate the three directors of node k by |w| h about w / |w| (unchanged if w = 0),
@@ -349,8 +384,12 @@ cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double*
                               cudaStream_t s)
 {
     if (L.N == 0) return cudaSuccess;
-    rod_segment_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, D, t_off);
-    rod_node_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, g64, m64, Xf, gf, mf);
+    if (L.chunks != nullptr) {
+        rod_forces_fused_kernel<<<L.n_chunks, kRodChunk, 0, s>>>(L, X, D, t_off, g64, m64, Xf, gf, mf);
+    } else {
+        rod_segment_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, D, t_off);
+        rod_node_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, g64, m64, Xf, gf, mf);
+    }
     if (L.p.lj_eps > 0.0) {
         const dim3 grid(nblk(L.nodes_per_inst, kLJTile), L.N / L.nodes_per_inst);
         rod_lj_kernel<<<grid, kLJTile, 0, s>>>(L, X, g64, gf);

@@ -279,6 +279,8 @@ cudaError_t admit_enqueue(mrs_server* S, SJob* j)
     L.dt = J.dt;
     L.p = J.params;
     L.FN = FN;
+    L.chunks = nullptr;   // two-kernel force path (no chunk table in the pool)
+    L.n_chunks = 0;
     return cudaSuccess;
 }
 
