@@ -660,6 +660,11 @@ def run_ours(args, world, rank, local, pg):
         "gpu_launches": args.steps,
         "wall_s_timed_region": wall,
     }
+    # the CPU baseline and the extras are single-GPU measurements reported at N = 1; with more
+    # ranks they would only hold the other GPUs idle
+    if world > 1:
+        args.cpu_baseline = False
+        args.extras = False
     if rank == 0 and args.cpu_baseline:
         import oracle
         nt, _ = oracle_rate(p, 10.0)
