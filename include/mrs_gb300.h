@@ -150,6 +150,13 @@ MRS_API int mrs_velocity_noalloc(int64_t n_points, const float* X, const float* 
 /* Explicit plans: build once, then execute many times (e.g. inside a CUDA graph).
  *   config  -1: the library's choice (tuned table or heuristic); otherwise an index into
  *           mrs_plan_config_count() kernel configurations (tile shape / targets per thread).
+ *           Configurations 17..30 are symmetric: when the targets are the sources (Xt NULL
+ *           or equal to X) each unordered pair {i, j} is evaluated once and serves both points
+ *           (the kernel values depend on |r| only and the reversed pair has separation -r),
+ *           and execution launches the persistent pair kernel plus a small deterministic
+ *           reduction kernel; with other targets such a plan runs an ordered configuration.
+ *           Their scratch holds one 6-vector per source slot of every work unit (about
+ *           N^2 / (2 TM) * 24 bytes for one system of N points, TM = 512 or 256).
  * A plan owns device tables and scratch; mrs_plan_execute allocates nothing and launches one
  * persistent kernel (or, for MRS_F64, one plain kernel).  Executions of the same plan must not
  * overlap on the GPU.  Arguments as for mrs_velocity. */
@@ -175,6 +182,9 @@ MRS_API int mrs_autotune_load(mrs_ctx* ctx, const char* path);
 /* Kernel configurations available to plans: count, and a description of entry `config`
  * (threads per CTA, targets per thread, CTAs resident per SM on this device). */
 MRS_API int mrs_plan_config_count(void);
+/* 1 if configuration `config` is symmetric (each unordered pair once; see mrs_plan_create),
+ * 0 if it is ordered, -1 if it is out of range.  Host only; no device call. */
+MRS_API int mrs_plan_config_symmetric(int config);
 MRS_API int mrs_plan_config_info(mrs_ctx* ctx, int config, int* threads, int* targets_per_thread,
                          int* ctas_per_sm);
 /* Grid size (persistent CTAs) and total work units of a plan, for reporting. */

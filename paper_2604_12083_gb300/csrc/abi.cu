@@ -46,10 +46,8 @@ static int check_offsets(int n_sys, const int64_t* off)
     return MRS_OK;
 }
 
-int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precision)
+int default_ordered_config(int n_sys, const int64_t* offsets)
 {
-    (void)ctx;
-    (void)precision;
     // Measured on GB300: the packed f32x2 variants are fastest.  256 threads x 2 targets
     // (512-target tiles) for systems of tens of thousands of points; 256 threads x 1 target with
     // the source loop unrolled twice (256-target tiles: more tiles, shorter fix-ups, less padding)
@@ -63,6 +61,100 @@ int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precisio
     return 9;
 }
 
+// Symmetric configuration used by default, and the largest scratch it may take by default.
+constexpr int kDefaultSymConfig = 24;
+constexpr double kSymScratchCap = 4.0 * 1024 * 1024 * 1024;
+
+// Work units and column-partial bytes of a symmetric plan with tiles of TM points.
+static double sym_units(int n_sys, const int64_t* offsets, int TM)
+{
+    double units = 0;
+    for (int s = 0; s < n_sys; ++s) {
+        const int64_t ns = offsets[s + 1] - offsets[s];
+        for (int64_t t = 0; t < ns; t += TM) units += (double)((ns - t + kUnitSources - 1) / kUnitSources);
+    }
+    return units;
+}
+
+int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precision)
+{
+    (void)precision;
+    // Measured on GB300: the symmetric kernel (each unordered pair once) beats the ordered
+    // ones when most pairs lie in systems of 8192 points or more and there are enough work
+    // units to keep every CTA of the persistent grid busy (a 4096-point system has ~600 units
+    // for ~450 CTAs and runs slower than the ordered kernel).  Its column partials grow as
+    // N^2 / TM, so it is not chosen by default beyond kSymScratchCap of scratch.
+    double big = 0, all = 0;
+    for (int s = 0; s < n_sys; ++s) {
+        const double ns = (double)(offsets[s + 1] - offsets[s]);
+        all += ns * ns;
+        if (ns >= 8192) big += ns * ns;
+    }
+    const KernelConfig kc = kConfigs[kDefaultSymConfig];
+    const double units = sym_units(n_sys, offsets, kc.threads * kc.tpt);
+    const double ctas = 3.0 * (ctx ? ctx->num_sms : 152);
+    if (all > 0 && big >= 0.5 * all && units >= 32.0 * ctas &&
+        units * kUnitSources * 6 * sizeof(float) <= kSymScratchCap)
+        return kDefaultSymConfig;
+    return default_ordered_config(n_sys, offsets);
+}
+
+// Work table of the symmetric path (see SymTile): one row per tile of TM points, from the
+// tile's first point to the end of its system; row segments are numbered tile by tile, one
+// per CTA whose unit range meets the row.
+static int sym_plan_build(mrs_plan* p, mrs_ctx* ctx, int cfg, const int64_t* offsets)
+{
+    const KernelConfig kc = kConfigs[cfg];
+    const int TM = kc.threads * kc.tpt;
+    std::vector<SymTile> tiles;
+    long long W = 0;
+    for (int s = 0; s < p->n_sys; ++s) {
+        const int64_t ns = offsets[s + 1] - offsets[s];
+        const int tfirst = (int)tiles.size();
+        for (int64_t t = 0, k = 0; t < ns; t += TM, ++k) {
+            SymTile T{};
+            T.sys = s;
+            T.t0 = (int)(offsets[s] + t);
+            T.tn = (int)std::min<int64_t>(TM, ns - t);
+            T.send = (int)offsets[s + 1];
+            T.nu = (int)((ns - t + kUnitSources - 1) / kUnitSources);
+            T.nd = (T.tn + kUnitSources - 1) / kUnitSources;
+            T.kt = (int)k;
+            T.tfirst = tfirst;
+            T.u0 = W;
+            tiles.push_back(T);
+            W += T.nu;
+        }
+    }
+    int occ = 0;
+    int st = occupancy_sym(cfg, p->precision == MRS_F32_COMP, &occ);
+    if (st != MRS_OK || occ < 1) {
+        set_error("occupancy query failed for config %d", cfg);
+        return MRS_ECUDA;
+    }
+    long long P = (long long)ctx->num_sms * occ;
+    if (P > W) P = W;
+    long long nseg = 0;
+    for (SymTile& T : tiles) {
+        T.qlo = cta_of_unit_host(W, (int)P, T.u0);
+        const int qhi = cta_of_unit_host(W, (int)P, T.u0 + T.nu - 1);
+        T.nseg = qhi - T.qlo + 1;
+        T.seg0 = (int)nseg;
+        nseg += T.nseg;
+    }
+    p->sym_config = cfg;
+    p->sP = (int)P;
+    p->sW = W;
+    p->s_tiles = (int)tiles.size();
+    p->sTM = TM;
+    if ((st = dev_alloc(&p->d_stiles, tiles.size())) ||
+        (st = dev_alloc(&p->d_rowpart, (size_t)nseg * TM * 6)) ||
+        (st = dev_alloc(&p->d_colpart, (size_t)W * kUnitSources * 6)))
+        return st;
+    cudaMemcpy(p->d_stiles, tiles.data(), tiles.size() * sizeof(SymTile), cudaMemcpyHostToDevice);
+    return MRS_OK;
+}
+
 void plan_free(mrs_plan* p)
 {
     if (!p) return;
@@ -74,6 +166,9 @@ void plan_free(mrs_plan* p)
     cudaFree(p->d_eps64);
     cudaFree(p->d_tile_sys);
     cudaFree(p->d_tile_t0);
+    cudaFree(p->d_stiles);
+    cudaFree(p->d_rowpart);
+    cudaFree(p->d_colpart);
     delete p;
 }
 
@@ -138,8 +233,9 @@ int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, doubl
     int cfg = config;
     if (cfg < 0) cfg = tuned_config(ctx, tune_key(n_sys, offsets, precision));
     if (cfg < 0) cfg = default_config(ctx, n_sys, offsets, precision);
-    const KernelConfig kc = kConfigs[cfg];
     p->config = cfg;
+    p->ocfg = kConfigs[cfg].sym ? default_ordered_config(n_sys, offsets) : cfg;
+    const KernelConfig kc = kConfigs[p->ocfg];
     p->TM = kc.threads * kc.tpt;
     std::vector<TileDesc> tiles;
     long long W = 0;
@@ -177,9 +273,9 @@ int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, doubl
         return MRS_OK;
     }
     int occ = 0;
-    if ((st = occupancy_f32(cfg, precision == MRS_F32_COMP, &occ)) != MRS_OK || occ < 1) {
+    if ((st = occupancy_f32(p->ocfg, precision == MRS_F32_COMP, &occ)) != MRS_OK || occ < 1) {
         plan_free(p);
-        set_error("occupancy query failed for config %d", cfg);
+        set_error("occupancy query failed for config %d", p->ocfg);
         return MRS_ECUDA;
     }
     long long P = (long long)ctx->num_sms * occ;
@@ -194,6 +290,10 @@ int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, doubl
     cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
     cudaMemcpy(p->d_sc, sc.data(), sc.size() * sizeof(SysConst), cudaMemcpyHostToDevice);
     cudaMemset(p->d_counters, 0, tiles.size() * sizeof(int));
+    if (kConfigs[cfg].sym && (st = sym_plan_build(p, ctx, cfg, offsets)) != MRS_OK) {
+        plan_free(p);
+        return st;
+    }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         plan_free(p);
@@ -261,7 +361,26 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
         L.partial = p->d_partial;
         L.counters = p->d_counters;
         L.err = p->ctx->d_err;
-        e = launch_mrs_f32(p->config, p->precision == MRS_F32_COMP, L, s);
+        if (p->sym_config >= 0 && (Xt == nullptr || Xt == X)) {
+            SymLaunch S;
+            S.tiles = p->d_stiles;
+            S.n_tiles = p->s_tiles;
+            S.TM = p->sTM;
+            S.W = p->sW;
+            S.P = p->sP;
+            S.sc = p->d_sc;
+            S.X = L.X;
+            S.f = L.f;
+            S.n = L.n;
+            S.u = L.u;
+            S.w = L.w;
+            S.rowpart = p->d_rowpart;
+            S.colpart = p->d_colpart;
+            S.err = L.err;
+            e = launch_mrs_sym(p->sym_config, p->precision == MRS_F32_COMP, S, s);
+        } else {
+            e = launch_mrs_f32(p->ocfg, p->precision == MRS_F32_COMP, L, s);
+        }
     }
     if (e != cudaSuccess) {
         set_error("pair-sum launch failed: %s", cudaGetErrorString(e));
@@ -368,6 +487,11 @@ int mrs_plan_destroy(mrs_plan* plan)
 
 int mrs_plan_config_count(void) { return kNumConfigs; }
 
+int mrs_plan_config_symmetric(int config)
+{
+    return (config >= 0 && config < kNumConfigs) ? kConfigs[config].sym : -1;
+}
+
 int mrs_plan_config_info(mrs_ctx* ctx, int config, int* threads, int* tpt, int* ctas_per_sm)
 {
     clear_error();
@@ -377,7 +501,8 @@ int mrs_plan_config_info(mrs_ctx* ctx, int config, int* threads, int* tpt, int* 
     if (ctas_per_sm) {
         MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
         MRS_CHECK_CUDA(cudaSetDevice(ctx->device));
-        int st = occupancy_f32(config, true, ctas_per_sm);
+        int st = kConfigs[config].sym ? occupancy_sym(config, true, ctas_per_sm)
+                                      : occupancy_f32(config, true, ctas_per_sm);
         if (st) return st;
     }
     return MRS_OK;
@@ -387,8 +512,9 @@ int mrs_plan_info(const mrs_plan* plan, int* grid, int64_t* work_units, int* con
 {
     clear_error();
     MRS_REQUIRE(plan != nullptr, "plan is NULL");
-    if (grid) *grid = plan->precision == MRS_F64 ? plan->n_blocks64 : plan->P;
-    if (work_units) *work_units = plan->W;
+    const bool sym = plan->precision != MRS_F64 && plan->sym_config >= 0;
+    if (grid) *grid = plan->precision == MRS_F64 ? plan->n_blocks64 : (sym ? plan->sP : plan->P);
+    if (work_units) *work_units = sym ? plan->sW : plan->W;
     if (config) *config = plan->config;
     return MRS_OK;
 }

@@ -72,6 +72,7 @@ struct KernelConfig {
     int paired;    // 1: packed f32x2 inner loop (two sources per instruction)
     int unroll;    // source-loop unroll of the packed loop (independent pair chains in flight)
     int sq;        // 1: s^2 = s*s by a packed multiply instead of an SFU reciprocal
+    int sym;       // 1: each unordered pair once (targets = sources only; mrs_sym.cu)
 };
 
 // Configurations compiled into the library (index = plan config id).
@@ -97,6 +98,60 @@ struct MrsLaunch {
 
 cudaError_t launch_mrs_f32(int config, bool comp, const MrsLaunch& L, cudaStream_t s);
 int occupancy_f32(int config, bool comp, int* ctas_per_sm);
+
+// ---------------------------------------------------------------------------------------------
+// Symmetric pair sum (targets = sources): every unordered pair {i, j} of a system is evaluated
+// once and contributes to both points.
+//
+// A system's points are cut into tiles of TM points.  The row of a tile holds the sources
+// from the tile's first point to the end of the system, cut into work units of kUnitSources
+// sources: the first nd units are the tile itself (the diagonal block, evaluated as ordered
+// pairs, each point as target only), the rest are later tiles (each unordered pair once: the
+// tile's points collect their share in registers, the source points' share is reduced over
+// the tile and written to a column partial).  As in the ordered kernel, CTA p of P processes
+// the contiguous unit range [W p / P, W (p+1) / P).  Every segment of a row processed by one
+// CTA writes a row partial; a second kernel sums, for every point, its row partials and the
+// column partials of all earlier tiles of its system in a fixed order (deterministic).
+// ---------------------------------------------------------------------------------------------
+constexpr int kSymChunk = 128;     // sources staged in shared memory at a time
+
+struct SymTile {
+    int sys;       // system index
+    int t0;        // first point of the tile (global point index)
+    int tn;        // points in the tile (1..TM)
+    int send;      // one past the system's last point (global point index)
+    int nu;        // work units of the row: ceil((send - t0) / kUnitSources)
+    int nd;        // diagonal units: ceil(tn / kUnitSources)
+    int kt;        // index of the tile within its system
+    int tfirst;    // global index of the system's first tile
+    int seg0;      // first row-partial slot of this tile
+    int nseg;      // number of CTAs (row segments) that process this row
+    int qlo;       // first CTA whose unit range meets the row
+    int pad_;
+    long long u0;  // global index of the row's first unit
+};
+
+struct SymLaunch {
+    const SymTile* tiles;
+    int n_tiles;
+    int TM;
+    long long W;          // total work units
+    int P;                // persistent CTAs
+    const SysConst* sc;
+    const float* X;
+    const float* f;
+    const float* n;
+    float* u;
+    float* w;
+    float* rowpart;       // [segments][TM][6]
+    float* colpart;       // [W * kUnitSources][6]: unit-major, one 6-vector per source slot
+    unsigned int* err;
+};
+
+cudaError_t launch_mrs_sym(int config, bool comp, const SymLaunch& L, cudaStream_t s);
+int occupancy_sym(int config, bool comp, int* ctas_per_sm);
+// The CTA (of P over W units) whose range contains unit x: host twin of the device search.
+int cta_of_unit_host(long long W, int P, long long x);
 
 struct MrsLaunch64 {
     int n_sys;
@@ -145,7 +200,8 @@ void rod_ws_free(RodWorkspace* ws);
 struct mrs_plan {
     mrs_ctx* ctx = nullptr;
     int precision = MRS_F32_COMP;
-    int config = 0;
+    int config = 0;               // the plan's configuration (symmetric or ordered)
+    int ocfg = 0;                 // ordered configuration (targets given apart from the sources)
     int n_sys = 0;
     int64_t n_points = 0;
     double mu = 1.0;
@@ -160,6 +216,15 @@ struct mrs_plan {
     mrs::SysConst* d_sc = nullptr;
     float* d_partial = nullptr;
     int* d_counters = nullptr;
+    // symmetric path (config with sym = 1; used when the targets are the sources)
+    int sym_config = -1;          // -1: no symmetric path; config then is the ordered one
+    int sP = 0;
+    int sTM = 0;
+    long long sW = 0;
+    int s_tiles = 0;
+    mrs::SymTile* d_stiles = nullptr;
+    float* d_rowpart = nullptr;
+    float* d_colpart = nullptr;
     // float64 path
     long long* d_off64 = nullptr;
     double* d_eps64 = nullptr;
@@ -192,5 +257,6 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
              void* w, cudaStream_t s);
 void plan_free(mrs_plan* p);
 int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precision);
+int default_ordered_config(int n_sys, const int64_t* offsets);
 int tuned_config(const mrs_ctx* ctx, const TuneKey& k);
 }  // namespace mrs

@@ -11,8 +11,9 @@
 //   8 pi H1 = s + e2 s3                      8 pi H2 = s3
 //   8 pi H3 = s3 + (3/2) e2 s5               8 pi H5 = s5 (3/2 + (15/4) e2 s2)
 //   8 pi H4 = s3 (-1/2 + s2 (-(3/4) e2 + (15/4) e2^2 s2))
-// so one pair costs 53 FP32 instructions (FFMA/FMUL/FADD) and 2 SFU instructions, and the
-// common factor 1/(8 pi mu) is applied once per target.  No tensor cores: the pair sum is not
+// and with the scaled separation H3 r serving both cross products (H3 (n x r) = n x (H3 r),
+// likewise for f), one pair costs 50 FP32 instructions (FFMA/FMUL/FADD) and 2 SFU
+// instructions; the common factor 1/(8 pi mu) is applied once per target.  No tensor cores: the pair sum is not
 // a dense contraction.
 //
 // Float32 path (MRS_F32 / MRS_F32_COMP): one persistent kernel over all systems of a batch.
@@ -31,23 +32,10 @@
 //
 // Float64 path (MRS_F64): one CTA per 128 targets, all sources of the system staged through
 // shared memory, float64 arithmetic with the kernels written in r^2.
+#include "mrs_device.cuh"
 #include "mrs_internal.h"
 
 namespace mrs {
-
-__device__ __forceinline__ float sfu_rsqrt(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float sfu_rcp(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // One (target, source) pair accumulated into acc[0..2] (u) and acc[3..5] (omega), both scaled
 // by 8 pi mu.  a = (X.x, X.y, X.z, f.x), b = (f.y, f.z, n.x, n.y), nz = n.z.
@@ -70,43 +58,40 @@ __device__ __forceinline__ void pair_f32(float xi, float yi, float zi, const flo
     const float nr = fmaf(nx, rx, fmaf(ny, ry, nz * rz));
     const float bf = s3 * fr;                                // 8 pi H2 (f.r)
     const float bn = h5 * nr;                                // 8 pi H5 (n.r)
+    // H3 (n x r) = n x (H3 r) and H3 (f x r) = f x (H3 r): one scaled separation serves both
+    const float hrx = h3 * rx, hry = h3 * ry, hrz = h3 * rz;
     // u += H1 f + H2 (f.r) r + H3 (n x r)
-    const float hnx = h3 * nx, hny = h3 * ny, hnz = h3 * nz;
     acc[0] = fmaf(h1, fx, acc[0]);
     acc[1] = fmaf(h1, fy, acc[1]);
     acc[2] = fmaf(h1, fz, acc[2]);
     acc[0] = fmaf(bf, rx, acc[0]);
     acc[1] = fmaf(bf, ry, acc[1]);
     acc[2] = fmaf(bf, rz, acc[2]);
-    acc[0] = fmaf(hny, rz, acc[0]);
-    acc[1] = fmaf(hnz, rx, acc[1]);
-    acc[2] = fmaf(hnx, ry, acc[2]);
-    acc[0] = fmaf(-hnz, ry, acc[0]);
-    acc[1] = fmaf(-hnx, rz, acc[1]);
-    acc[2] = fmaf(-hny, rx, acc[2]);
+    acc[0] = fmaf(ny, hrz, acc[0]);
+    acc[1] = fmaf(nz, hrx, acc[1]);
+    acc[2] = fmaf(nx, hry, acc[2]);
+    acc[0] = fmaf(-nz, hry, acc[0]);
+    acc[1] = fmaf(-nx, hrz, acc[1]);
+    acc[2] = fmaf(-ny, hrx, acc[2]);
     // omega += H3 (f x r) + H4 n + H5 (n.r) r
-    const float hfx = h3 * fx, hfy = h3 * fy, hfz = h3 * fz;
     acc[3] = fmaf(h4, nx, acc[3]);
     acc[4] = fmaf(h4, ny, acc[4]);
     acc[5] = fmaf(h4, nz, acc[5]);
     acc[3] = fmaf(bn, rx, acc[3]);
     acc[4] = fmaf(bn, ry, acc[4]);
     acc[5] = fmaf(bn, rz, acc[5]);
-    acc[3] = fmaf(hfy, rz, acc[3]);
-    acc[4] = fmaf(hfz, rx, acc[4]);
-    acc[5] = fmaf(hfx, ry, acc[5]);
-    acc[3] = fmaf(-hfz, ry, acc[3]);
-    acc[4] = fmaf(-hfx, rz, acc[4]);
-    acc[5] = fmaf(-hfy, rx, acc[5]);
+    acc[3] = fmaf(fy, hrz, acc[3]);
+    acc[4] = fmaf(fz, hrx, acc[4]);
+    acc[5] = fmaf(fx, hry, acc[5]);
+    acc[3] = fmaf(-fz, hry, acc[3]);
+    acc[4] = fmaf(-fx, hrz, acc[4]);
+    acc[5] = fmaf(-fy, hrx, acc[5]);
 }
 
 // Packed form of pair_f32: the two lanes of every float2 hold two different sources (j, j+1)
 // for the same target, so each f32x2 instruction does the work of two scalar ones.  q = X - x
 // (the negated separation; every term below is written in q: (f.r) r = (f.q) q and
 // n x r = q x n), so the staged positions need no negation.
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-
 template <bool SQ>
 __device__ __forceinline__ void pair_f32x2(const float2 xt, const float2 yt, const float2 zt,  // targets
                                            const float2 X0, const float2 X1, const float2 X2,
@@ -131,7 +116,8 @@ __device__ __forceinline__ void pair_f32x2(const float2 xt, const float2 yt, con
     const float2 nq = __ffma2_rn(N0, qx, __ffma2_rn(N1, qy, __fmul2_rn(N2, qz)));
     const float2 bf = __fmul2_rn(s3, fq);
     const float2 bn = __fmul2_rn(h5, nq);
-    const float2 hn0 = __fmul2_rn(h3, N0), hn1 = __fmul2_rn(h3, N1), hn2 = __fmul2_rn(h3, N2);
+    // H3 (q x n) = (H3 q) x n and H3 (q x f) = (H3 q) x f: one scaled separation serves both
+    const float2 hq0 = __fmul2_rn(h3, qx), hq1 = __fmul2_rn(h3, qy), hq2 = __fmul2_rn(h3, qz);
     // u += H1 f + H2 (f.q) q + H3 (q x n)
     acc[0] = __ffma2_rn(h1, F0, acc[0]);
     acc[1] = __ffma2_rn(h1, F1, acc[1]);
@@ -139,40 +125,25 @@ __device__ __forceinline__ void pair_f32x2(const float2 xt, const float2 yt, con
     acc[0] = __ffma2_rn(bf, qx, acc[0]);
     acc[1] = __ffma2_rn(bf, qy, acc[1]);
     acc[2] = __ffma2_rn(bf, qz, acc[2]);
-    acc[0] = __ffma2_rn(qy, hn2, acc[0]);
-    acc[1] = __ffma2_rn(qz, hn0, acc[1]);
-    acc[2] = __ffma2_rn(qx, hn1, acc[2]);
-    acc[0] = __ffma2_rn(neg2(qz), hn1, acc[0]);
-    acc[1] = __ffma2_rn(neg2(qx), hn2, acc[1]);
-    acc[2] = __ffma2_rn(neg2(qy), hn0, acc[2]);
+    acc[0] = __ffma2_rn(hq1, N2, acc[0]);
+    acc[1] = __ffma2_rn(hq2, N0, acc[1]);
+    acc[2] = __ffma2_rn(hq0, N1, acc[2]);
+    acc[0] = __ffma2_rn(neg2(hq2), N1, acc[0]);
+    acc[1] = __ffma2_rn(neg2(hq0), N2, acc[1]);
+    acc[2] = __ffma2_rn(neg2(hq1), N0, acc[2]);
     // omega += H3 (q x f) + H4 n + H5 (n.q) q
-    const float2 hf0 = __fmul2_rn(h3, F0), hf1 = __fmul2_rn(h3, F1), hf2 = __fmul2_rn(h3, F2);
     acc[3] = __ffma2_rn(h4, N0, acc[3]);
     acc[4] = __ffma2_rn(h4, N1, acc[4]);
     acc[5] = __ffma2_rn(h4, N2, acc[5]);
     acc[3] = __ffma2_rn(bn, qx, acc[3]);
     acc[4] = __ffma2_rn(bn, qy, acc[4]);
     acc[5] = __ffma2_rn(bn, qz, acc[5]);
-    acc[3] = __ffma2_rn(qy, hf2, acc[3]);
-    acc[4] = __ffma2_rn(qz, hf0, acc[4]);
-    acc[5] = __ffma2_rn(qx, hf1, acc[5]);
-    acc[3] = __ffma2_rn(neg2(qz), hf1, acc[3]);
-    acc[4] = __ffma2_rn(neg2(qx), hf2, acc[4]);
-    acc[5] = __ffma2_rn(neg2(qy), hf0, acc[5]);
-}
-
-// Kahan step: (sum, comp) += v, with sum - comp the compensated total.
-__device__ __forceinline__ void kahan_add(float& sum, float& comp, float v)
-{
-    const float y = __fsub_rn(v, comp);
-    const float t = __fadd_rn(sum, y);
-    comp = __fsub_rn(__fsub_rn(t, sum), y);
-    sum = t;
-}
-
-__device__ __forceinline__ long long unit_start(long long W, int P, int p)
-{
-    return (W * (long long)p) / (long long)P;
+    acc[3] = __ffma2_rn(hq1, F2, acc[3]);
+    acc[4] = __ffma2_rn(hq2, F0, acc[4]);
+    acc[5] = __ffma2_rn(hq0, F1, acc[5]);
+    acc[3] = __ffma2_rn(neg2(hq2), F1, acc[3]);
+    acc[4] = __ffma2_rn(neg2(hq0), F2, acc[4]);
+    acc[5] = __ffma2_rn(neg2(hq1), F0, acc[5]);
 }
 
 // The CTA whose unit range contains unit x.
@@ -463,6 +434,11 @@ const KernelConfig kConfigs[] = {
     {128, 2, 1, 1}, {128, 4, 1, 1}, {64, 4, 1, 1}, {256, 2, 1, 1},
     {256, 2, 1, 2}, {128, 2, 1, 2}, {128, 1, 1, 1}, {128, 1, 1, 2}, {256, 1, 1, 2},
     {256, 2, 1, 1, 1}, {256, 1, 1, 2, 1},
+    // symmetric (mrs_sym.cu): packs of two points per thread, duplicated sources
+    {128, 4, 1, 1, 0, 1}, {128, 2, 1, 1, 0, 1}, {64, 4, 1, 1, 0, 1}, {128, 4, 1, 1, 1, 1},
+    {128, 4, 1, 1, 0, 1}, {128, 2, 1, 1, 0, 1}, {64, 4, 1, 1, 0, 1}, {128, 4, 1, 1, 1, 1},
+    {384, 4, 1, 1, 0, 1}, {384, 4, 1, 1, 1, 1},
+    {128, 4, 1, 1, 1, 1}, {128, 4, 1, 2, 1, 1}, {128, 6, 1, 1, 1, 1}, {128, 4, 1, 4, 1, 1},
 };
 const int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 

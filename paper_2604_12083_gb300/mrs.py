@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "MRS_OK", 1: "MRS_EINVAL", 2: "MRS_ENOMEM", 3: "MRS_ECUDA", 4
 EXPORTS = [
     "mrs_last_error", "mrs_version", "mrs_ctx_create", "mrs_ctx_destroy", "mrs_ctx_num_sms",
     "mrs_velocity", "mrs_plan_create", "mrs_plan_execute", "mrs_plan_destroy",
-    "mrs_plan_config_count", "mrs_plan_config_info", "mrs_plan_info",
+    "mrs_plan_config_count", "mrs_plan_config_symmetric", "mrs_plan_config_info", "mrs_plan_info",
     "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run", "mrs_velocity_noalloc",
     "serve_create", "serve_submit", "serve_poll", "serve_drain", "serve_stats", "serve_destroy",
     "serve_cancel",
@@ -289,6 +289,14 @@ def autotune_load(ctx: Context, path: str):
 
 def plan_config_count() -> int:
     return int(lib().mrs_plan_config_count())
+
+
+def plan_config_symmetric(config: int) -> bool:
+    """``mrs_plan_config_symmetric``: whether a configuration evaluates each unordered pair once."""
+    r = int(lib().mrs_plan_config_symmetric(int(config)))
+    if r < 0:
+        raise MrsError(MRS_EINVAL, "config %d out of range" % config)
+    return bool(r)
 
 
 def plan_config_info(ctx: Context, config: int):

@@ -98,7 +98,11 @@ def ragged_batch():
     return W.MRSProblem("ragged", off, f32(Xs), f32(fs), f32(ns), eps, 1.3)
 
 
-@pytest.mark.parametrize("config", list(range(17)))
+N_CONFIGS = 31          # ordered configurations 0..16, symmetric (pair-reuse) 17..30
+SYM_CONFIGS = list(range(17, 31))
+
+
+@pytest.mark.parametrize("config", list(range(N_CONFIGS)))
 @pytest.mark.parametrize("precision", [1, 2])
 def test_ragged_batch_every_config(ctx, orc, config, precision):
     p = ragged_batch()
@@ -133,42 +137,75 @@ def test_separate_targets(ctx, orc):
     assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
 
 
-def test_multi_tile_single_system(ctx, orc):
-    """A few thousand points: several tiles, every tile split over many CTAs (fix-up path)."""
+@pytest.mark.parametrize("config", [None] + SYM_CONFIGS)
+def test_multi_tile_single_system(ctx, orc, config):
+    """A few thousand points: several tiles, every tile split over many CTAs (fix-up path;
+    for the symmetric configurations, rows split over many CTAs and many column partials)."""
     from paper_2604_12083_gb300 import mrs, workloads as W
     p = W.single_system(seed=62, n_fil=3, M=1000)      # 3000 points, ragged last tile
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
     for prec in (mrs.MRS_F32, mrs.MRS_F32_COMP):
-        u, w = run(ctx, p, prec)
-        ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+        u, w = run(ctx, p, prec, config=config)
         assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
 
 
-def test_deterministic(ctx):
+@pytest.mark.parametrize("config", SYM_CONFIGS)
+def test_symmetric_plan_with_targets(ctx, orc, config):
+    """A symmetric plan given targets equal to the sources (the same buffer) takes the
+    symmetric path; given other targets it takes the ordered path.  Both match the oracle."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.single_system(seed=69, n_fil=2, M=900)
+    dt = torch.float32
+    X, f, n = dev(p.X, dt), dev(p.f, dt), dev(p.n, dt)
+    pl = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32_COMP,
+                  config=config)
+    assert pl.info()["config"] == config
+    u, w = torch.full_like(X, float("nan")), torch.full_like(X, float("nan"))
+    pl.execute(X, f, n, u, w, Xt=X)
+    torch.cuda.synchronize()
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+    assert rel_l2(u.cpu().numpy(), ur) < TOL32 and rel_l2(w.cpu().numpy(), wr) < TOL32
+    rng = np.random.default_rng(69)
+    Xt = (p.X + rng.normal(0, 0.01, p.X.shape)).astype(np.float32)
+    u2, w2 = torch.full_like(X, float("nan")), torch.full_like(X, float("nan"))
+    pl.execute(X, f, n, u2, w2, Xt=dev(Xt, dt))
+    torch.cuda.synchronize()
+    pl.close()
+    ur2, wr2 = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu, xt=Xt)
+    assert rel_l2(u2.cpu().numpy(), ur2) < TOL32 and rel_l2(w2.cpu().numpy(), wr2) < TOL32
+
+
+@pytest.mark.parametrize("config", [None, 17])
+def test_deterministic(ctx, config):
+    """Bit-identical results on repeated calls: fixed summation orders, no float atomics."""
     from paper_2604_12083_gb300 import mrs, workloads as W
     p = W.single_system(seed=63, n_fil=4, M=1024)
-    a = run(ctx, p, mrs.MRS_F32_COMP)
-    b = run(ctx, p, mrs.MRS_F32_COMP)
+    a = run(ctx, p, mrs.MRS_F32_COMP, config=config)
+    b = run(ctx, p, mrs.MRS_F32_COMP, config=config)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
-def test_full_size_single_system_sampled(ctx, orc):
-    """32 filaments x 1024 nodes, the benchmark's launch (cached plan, default config): 512
-    sampled targets against all 32768 sources, computed one by one by the oracle."""
+@pytest.mark.parametrize("config", [None, 17])
+def test_full_size_single_system_sampled(ctx, orc, config):
+    """32 filaments x 1024 nodes, the benchmark's launch (cached plan, default config; and the
+    symmetric configuration): 512 sampled targets against all 32768 sources, computed one by
+    one by the oracle."""
     from paper_2604_12083_gb300 import mrs, workloads as W
     p = W.single_system()
-    u, w = run(ctx, p, mrs.MRS_F32_COMP)
+    u, w = run(ctx, p, mrs.MRS_F32_COMP, config=config)
     assert np.isfinite(u).all() and np.isfinite(w).all()
     idx = np.random.default_rng(64).choice(p.n_points, 512, replace=False)
     ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu, xt=p.X[idx])
     assert rel_l2(u[idx], ur) < TOL32 and rel_l2(w[idx], wr) < TOL32
 
 
-def test_full_size_batch_sampled(ctx, orc):
+@pytest.mark.parametrize("config", [None, 17])
+def test_full_size_batch_sampled(ctx, orc, config):
     """512 systems of 256..16384 points in one persistent launch: 4 sampled targets per system
     against all sources of their own system."""
     from paper_2604_12083_gb300 import mrs, workloads as W
     p = W.batch_systems()
-    u, w = run(ctx, p, mrs.MRS_F32)
+    u, w = run(ctx, p, mrs.MRS_F32, config=config)
     rng = np.random.default_rng(65)
     eu_n = eu_d = ew_n = ew_d = 0.0
     for s in range(len(p.offsets) - 1):
@@ -228,8 +265,8 @@ def test_autotune_picks_a_config_used_by_plans(ctx, orc, tmp_path):
 def test_config_table_size(ctx):
     """Every compiled configuration is covered by the ragged-batch parity test above."""
     from paper_2604_12083_gb300 import mrs
-    assert mrs.plan_config_count() == 17
-    for c in range(17):
+    assert mrs.plan_config_count() == N_CONFIGS
+    for c in range(N_CONFIGS):
         info = mrs.plan_config_info(ctx, c)
         assert info["ctas_per_sm"] >= 1
 
@@ -251,7 +288,8 @@ def test_nonfinite_inputs_raise_the_device_flag(ctx):
         assert ctx.device_status() == 0
 
 
-def test_large_ragged_single_system_sampled(ctx, orc):
+@pytest.mark.parametrize("config", [None, 17])
+def test_large_ragged_single_system_sampled(ctx, orc, config):
     """2^18 + 17 points (6.9e10 pairs, a ragged last tile): 256 sampled targets against all
     sources, computed one by one by the oracle."""
     from paper_2604_12083_gb300 import mrs, workloads as W
@@ -261,7 +299,7 @@ def test_large_ragged_single_system_sampled(ctx, orc):
     f = rng.standard_normal((N, 3)).astype(np.float32)
     n = rng.standard_normal((N, 3)).astype(np.float32)
     p = W.MRSProblem("large", np.array([0, N], np.int64), X, f, n, np.array([0.02]), 1.0)
-    u, w = run(ctx, p, mrs.MRS_F32_COMP)
+    u, w = run(ctx, p, mrs.MRS_F32_COMP, config=config)
     idx = np.concatenate([rng.choice(N, 250, replace=False), np.arange(N - 6, N)])
     ur, wr = orc.mrs_velocity(p.X, p.f, p.n, 0.02, 1.0, xt=p.X[idx])
     assert rel_l2(u[idx], ur) < TOL32 and rel_l2(w[idx], wr) < TOL32
