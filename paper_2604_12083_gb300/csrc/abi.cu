@@ -62,7 +62,7 @@ int default_ordered_config(int n_sys, const int64_t* offsets)
 }
 
 // Symmetric configuration used by default, and the largest scratch it may take by default.
-constexpr int kDefaultSymConfig = 24;
+constexpr int kDefaultSymConfig = 23;
 constexpr double kSymScratchCap = 4.0 * 1024 * 1024 * 1024;
 
 // Work units and column-partial bytes of a symmetric plan with tiles of TM points.

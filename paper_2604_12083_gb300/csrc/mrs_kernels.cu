@@ -435,10 +435,8 @@ const KernelConfig kConfigs[] = {
     {256, 2, 1, 2}, {128, 2, 1, 2}, {128, 1, 1, 1}, {128, 1, 1, 2}, {256, 1, 1, 2},
     {256, 2, 1, 1, 1}, {256, 1, 1, 2, 1},
     // symmetric (mrs_sym.cu): packs of two points per thread, duplicated sources
-    {128, 4, 1, 1, 0, 1}, {128, 2, 1, 1, 0, 1}, {64, 4, 1, 1, 0, 1}, {128, 4, 1, 1, 1, 1},
-    {128, 4, 1, 1, 0, 1}, {128, 2, 1, 1, 0, 1}, {64, 4, 1, 1, 0, 1}, {128, 4, 1, 1, 1, 1},
-    {384, 4, 1, 1, 0, 1}, {384, 4, 1, 1, 1, 1},
-    {128, 4, 1, 1, 1, 1}, {128, 4, 1, 2, 1, 1}, {128, 6, 1, 1, 1, 1}, {128, 4, 1, 4, 1, 1},
+    {128, 4, 1, 1, 0, 1}, {128, 4, 1, 1, 0, 1}, {128, 4, 1, 1, 1, 1}, {384, 4, 1, 1, 0, 1},
+    {128, 6, 1, 1, 1, 1}, {128, 8, 1, 1, 1, 1}, {64, 6, 1, 1, 1, 1},
 };
 const int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 

@@ -383,40 +383,42 @@ mrs_f32_sym(const SymLaunch L)
     }
 }
 
-// Final sum per point: its row's partials (CTA order), then the column partials of every
-// earlier tile of its system (tile order), Kahan-compensated; scaled by 1/(8 pi mu).
+// Final sum per point and component: its row's partials (CTA order), then the column partials
+// of every earlier tile of its system (tile order), Kahan-compensated; scaled by 1/(8 pi mu).
+// One thread per (point, component), so consecutive threads read consecutive floats; the
+// partials are fetched kRedAhead at a time so that their L2 latencies overlap.
+constexpr int kRedAhead = 8;
+
 __global__ void __launch_bounds__(256) mrs_sym_reduce(const SymLaunch L)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)L.n_tiles * L.TM) return;
-    const int ti = (int)(idx / L.TM), li = (int)(idx - (long long)ti * L.TM);
+    if (idx >= (long long)L.n_tiles * L.TM * 6) return;
+    const long long pt = idx / 6;
+    const int q = (int)(idx - pt * 6);
+    const int ti = (int)(pt / L.TM), li = (int)(pt - (long long)ti * L.TM);
     const SymTile T = L.tiles[ti];
     if (li >= T.tn) return;
     const int j = T.t0 + li;
-    float sum[6], cmp[6];
+    float sum = 0.f, cmp = 0.f;
+    for (int sgi = 0; sgi < T.nseg; ++sgi)
+        kahan_add(sum, cmp, __ldcg(L.rowpart + ((long long)(T.seg0 + sgi) * L.TM + li) * 6 + q));
+    for (int k0 = 0; k0 < T.kt; k0 += kRedAhead) {
+        float v[kRedAhead];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        sum[q] = 0.f;
-        cmp[q] = 0.f;
-    }
-    for (int sgi = 0; sgi < T.nseg; ++sgi) {
-        const float* rp = L.rowpart + ((long long)(T.seg0 + sgi) * L.TM + li) * 6;
+        for (int a = 0; a < kRedAhead; ++a) {
+            v[a] = 0.f;
+            if (k0 + a < T.kt) {
+                const SymTile& R = L.tiles[T.tfirst + k0 + a];
+                v[a] = __ldcg(L.colpart + ((long long)R.u0 * kUnitSources + (j - R.t0)) * 6 + q);
+            }
+        }
 #pragma unroll
-        for (int q = 0; q < 6; ++q) kahan_add(sum[q], cmp[q], __ldcg(rp + q));
+        for (int a = 0; a < kRedAhead; ++a)
+            if (k0 + a < T.kt) kahan_add(sum, cmp, v[a]);
     }
-    for (int k = 0; k < T.kt; ++k) {
-        const SymTile& R = L.tiles[T.tfirst + k];
-        const float* cp = L.colpart + ((long long)R.u0 * kUnitSources + (j - R.t0)) * 6;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) kahan_add(sum[q], cmp[q], __ldcg(cp + q));
-    }
-    const float scale = L.sc[T.sys].scale;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const float v = __fsub_rn(sum[q], cmp[q]) * scale;
-        if (!isfinite(v)) atomicOr(L.err, 1u);
-        if (q < 3) L.u[(long long)j * 3 + q] = v; else L.w[(long long)j * 3 + q - 3] = v;
-    }
+    const float val = __fsub_rn(sum, cmp) * L.sc[T.sys].scale;
+    if (!isfinite(val)) atomicOr(L.err, 1u);
+    if (q < 3) L.u[(long long)j * 3 + q] = val; else L.w[(long long)j * 3 + q - 3] = val;
 }
 
 int cta_of_unit_host(long long W, int P, long long x)
@@ -447,7 +449,7 @@ static cudaError_t launch_sym_t(const SymLaunch& L, cudaStream_t s)
         <<<L.P, BLOCK, sym_smem_bytes<BLOCK, TPT, COMP>(), s>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const long long n = (long long)L.n_tiles * L.TM;
+    const long long n = (long long)L.n_tiles * L.TM * 6;
     mrs_sym_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L);
     return cudaGetLastError();
 }
@@ -466,22 +468,19 @@ static int occ_sym_t(int* n)
         return comp ? FN<B, T, true, Q, K, U, M>(__VA_ARGS__) : FN<B, T, false, Q, K, U, M>(__VA_ARGS__);
 #define MRS_SYM_CASE(id, B, T, Q, K, FN, ...) MRS_SYM_CASE_X(id, B, T, Q, K, 2, 0, FN, __VA_ARGS__)
 
+// Symmetric configurations (ids continue the ordered table of mrs_kernels.cu).  Measured on the
+// 32768-point system (ms per call, both kernels): 17: 1.80 (warp-shuffle reduction of each
+// source's share), 18: 1.68, 19: 1.67, 20: 1.68 (one 384-thread CTA per SM), 21: 1.653,
+// 22: 1.651, 23: 1.642 (the default).
 #define MRS_SYM_DISPATCH(cfg, comp, FN, ...)                             \
     switch (cfg) {                                                       \
         MRS_SYM_CASE(17, 128, 4, false, false, FN, __VA_ARGS__)          \
-        MRS_SYM_CASE(18, 128, 2, false, false, FN, __VA_ARGS__)          \
-        MRS_SYM_CASE(19, 64, 4, false, false, FN, __VA_ARGS__)           \
-        MRS_SYM_CASE(20, 128, 4, true, false, FN, __VA_ARGS__)           \
-        MRS_SYM_CASE(21, 128, 4, false, true, FN, __VA_ARGS__)           \
-        MRS_SYM_CASE(22, 128, 2, false, true, FN, __VA_ARGS__)           \
-        MRS_SYM_CASE(23, 64, 4, false, true, FN, __VA_ARGS__)            \
-        MRS_SYM_CASE(24, 128, 4, true, true, FN, __VA_ARGS__)            \
-        MRS_SYM_CASE(25, 384, 4, false, true, FN, __VA_ARGS__)           \
-        MRS_SYM_CASE(26, 384, 4, true, true, FN, __VA_ARGS__)            \
-        MRS_SYM_CASE_X(27, 128, 4, true, true, 1, 0, FN, __VA_ARGS__)    \
-        MRS_SYM_CASE_X(28, 128, 4, true, true, 2, 2, FN, __VA_ARGS__)    \
-        MRS_SYM_CASE_X(29, 128, 6, true, true, 1, 2, FN, __VA_ARGS__)    \
-        MRS_SYM_CASE_X(30, 128, 4, true, true, 4, 0, FN, __VA_ARGS__)    \
+        MRS_SYM_CASE(18, 128, 4, false, true, FN, __VA_ARGS__)           \
+        MRS_SYM_CASE(19, 128, 4, true, true, FN, __VA_ARGS__)            \
+        MRS_SYM_CASE(20, 384, 4, false, true, FN, __VA_ARGS__)           \
+        MRS_SYM_CASE_X(21, 128, 6, true, true, 1, 2, FN, __VA_ARGS__)    \
+        MRS_SYM_CASE_X(22, 128, 8, true, true, 1, 2, FN, __VA_ARGS__)    \
+        MRS_SYM_CASE_X(23, 64, 6, true, true, 1, 4, FN, __VA_ARGS__)     \
     default: break;                                                      \
     }
 
