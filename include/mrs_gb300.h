@@ -150,7 +150,7 @@ MRS_API int mrs_velocity_noalloc(int64_t n_points, const float* X, const float* 
 /* Explicit plans: build once, then execute many times (e.g. inside a CUDA graph).
  *   config  -1: the library's choice (tuned table or heuristic); otherwise an index into
  *           mrs_plan_config_count() kernel configurations (tile shape / targets per thread).
- *           Configurations 17..30 are symmetric: when the targets are the sources (Xt NULL
+ *           Configurations 17..23 are symmetric: when the targets are the sources (Xt NULL
  *           or equal to X) each unordered pair {i, j} is evaluated once and serves both points
  *           (the kernel values depend on |r| only and the reversed pair has separation -r),
  *           and execution launches the persistent pair kernel plus a small deterministic
@@ -360,9 +360,12 @@ MRS_API int serve_cancel(mrs_server* srv, uint64_t ticket);
 MRS_API int serve_drain(mrs_server* srv, double timeout_s);
 
 /* Counters: iterations run, jobs completed, pair interactions computed, peak jobs admitted at
- * once, peak pool bytes in use. */
+ * once, peak pool bytes in use, and the iterations whose batched pair sum ran the symmetric
+ * kernel (each unordered pair once; the others ran the ordered kernel because the iteration's
+ * partial sums did not fit the server's scratch: 3 % of hbm_budget_bytes, at most 3 GiB, carved
+ * from the budget).  Any output pointer may be NULL. */
 MRS_API int serve_stats(mrs_server* srv, int64_t* iterations, int64_t* completed, double* pairs,
-                        int* peak_active, size_t* peak_pool_bytes);
+                        int* peak_active, size_t* peak_pool_bytes, int64_t* symmetric_iterations);
 
 /* Stop the scheduler (after the queued work finishes) and free the pool. */
 MRS_API int serve_destroy(mrs_server* srv);

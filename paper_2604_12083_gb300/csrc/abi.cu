@@ -49,15 +49,17 @@ static int check_offsets(int n_sys, const int64_t* off)
 int default_ordered_config(int n_sys, const int64_t* offsets)
 {
     // Measured on GB300: the packed f32x2 variants are fastest.  256 threads x 2 targets
-    // (512-target tiles) for systems of tens of thousands of points; 256 threads x 1 target with
-    // the source loop unrolled twice (256-target tiles: more tiles, shorter fix-ups, less padding)
-    // when most points sit in systems of at most 8192 points.  mrs_autotune overrides both.
+    // (512-target tiles) for systems of tens of thousands of points; when most points sit in
+    // systems of at most 8192 points, 256 threads x 1 target with the source loop unrolled twice
+    // for a few systems (a single 4096-point system: 45 us against 59 us), and 64 threads x 4
+    // targets (256-target tiles, 8 CTAs per SM) for many (64 systems of 4096 points: 1.69 ms
+    // against 1.77 ms).  mrs_autotune overrides all three.
     int64_t small = 0, total = offsets[n_sys];
     for (int s = 0; s < n_sys; ++s) {
         const int64_t ns = offsets[s + 1] - offsets[s];
         if (ns <= 8192) small += ns;
     }
-    if (total > 0 && small * 2 > total) return 14;
+    if (total > 0 && small * 2 > total) return n_sys >= 16 ? 8 : 14;
     return 9;
 }
 

@@ -7,7 +7,9 @@
 //   2. for every admitted rod job, computes its rod forces for the current stage and packs
 //      positions, forces and torques (float32) into the job's range of the point pool;
 //   3. runs ONE persistent pair-sum launch over all admitted jobs (each job one system of the
-//      batch, its own eps and mu) -- the work of every job in flight overlaps on the GPU;
+//      batch, its own eps and mu) -- the work of every job in flight overlaps on the GPU.  The
+//      launch is the symmetric kernel (each unordered pair once, mrs_sym.cu) whenever the
+//      iteration's row and column partials fit the server's scratch, else the ordered one;
 //   4. velocity jobs copy their result out and finish; rod jobs apply the stage's update and
 //      finish after their last step (state copied back to the caller).
 // At most two iterations are in flight: the host builds iteration i+1 while the GPU runs i, and
@@ -87,6 +89,9 @@ class RangeAlloc {
 
 constexpr int kMaxRodsPerJob = 1024;
 constexpr int kServeConfig = 8;             // 64 threads x 4 targets, packed f32x2 (TM = 256)
+constexpr int kServeSymConfig = 23;         // symmetric, 64 threads x 6 points (TM = 384)
+constexpr double kServeSymShare = 0.03;     // share of the budget for symmetric scratch ...
+constexpr size_t kServeSymMax = (size_t)3 << 30;   // ... up to 3 GiB
 constexpr int kMaxServeTiles = 1 << 20;     // tiles of one iteration's batched launch
 constexpr size_t kByteAlign = 256;
 
@@ -155,8 +160,16 @@ struct mrs_server {
     SysConst* d_sc = nullptr;
     float* d_partial = nullptr;
     int* d_counters = nullptr;
+    // symmetric launch: work table and row / column partials (capacities in floats)
+    int sym_config = 0, sTM = 0, sP = 0;
+    SymTile* d_stiles = nullptr;
+    float* d_rowpart = nullptr;
+    float* d_colpart = nullptr;
+    size_t rowpart_cap = 0, colpart_cap = 0;
+    int64_t sym_iterations = 0;
     struct Stage {
         TileDesc* tiles = nullptr;
+        SymTile* stiles = nullptr;
         SysConst* sc = nullptr;
         cudaEvent_t used = nullptr;
     } stage[3];
@@ -303,25 +316,10 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
     mrs_server::Stage& st = S->stage[S->stage_idx];
     S->stage_idx = (S->stage_idx + 1) % 3;
     if ((e = cudaEventSynchronize(st.used))) return e;   // the staging buffer is free again
-    int nt = 0;
-    long long W = 0;
-    double pairs = 0.0;
     const int n_sys = (int)S->active.size();
+    double pairs = 0.0;
     for (int q = 0; q < n_sys; ++q) {
         SJob* j = S->active[q];
-        const long long N = j->spec.n_points;
-        const int nu = (int)((N + kUnitSources - 1) / kUnitSources);
-        for (long long t = 0; t < N; t += S->TM) {
-            TileDesc& T = st.tiles[nt++];
-            T.sys = q;
-            T.t0 = (int)(j->pt_off + t);
-            T.tn = (int)std::min<long long>(S->TM, N - t);
-            T.s0 = (int)j->pt_off;
-            T.sn = (int)N;
-            T.nu = nu;
-            T.u0 = W;
-            W += nu;
-        }
         const double e2 = j->spec.eps * j->spec.eps;
         SysConst& c = st.sc[q];
         c.e2 = (float)e2;
@@ -330,27 +328,101 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
         c.c3 = (float)(-0.75 * e2);
         c.c5 = (float)(3.75 * e2);
         c.scale = (float)(1.0 / (8.0 * M_PI * j->spec.mu));
-        pairs += (double)N * (double)N;
+        pairs += (double)j->spec.n_points * (double)j->spec.n_points;
     }
-    if ((e = cudaMemcpyAsync(S->d_tiles, st.tiles, nt * sizeof(TileDesc), cudaMemcpyHostToDevice, s))) return e;
+    // symmetric work table (see SymTile), used when its partials fit the scratch
+    int snt = 0;
+    long long sW = 0;
+    for (int q = 0; q < n_sys; ++q) {
+        SJob* j = S->active[q];
+        const long long N = j->spec.n_points;
+        const int tfirst = snt;
+        for (long long t = 0, k = 0; t < N; t += S->sTM, ++k) {
+            SymTile& T = st.stiles[snt++];
+            T = SymTile{};
+            T.sys = q;
+            T.t0 = (int)(j->pt_off + t);
+            T.tn = (int)std::min<long long>(S->sTM, N - t);
+            T.send = (int)(j->pt_off + N);
+            T.nu = (int)((N - t + kUnitSources - 1) / kUnitSources);
+            T.nd = (T.tn + kUnitSources - 1) / kUnitSources;
+            T.kt = (int)k;
+            T.tfirst = tfirst;
+            T.u0 = sW;
+            sW += T.nu;
+        }
+    }
+    const int sP = (int)std::min<long long>(S->sP, sW);
+    long long nseg = 0;
+    for (int i = 0; i < snt; ++i) {
+        SymTile& T = st.stiles[i];
+        T.qlo = cta_of_unit_host(sW, sP, T.u0);
+        T.nseg = cta_of_unit_host(sW, sP, T.u0 + T.nu - 1) - T.qlo + 1;
+        T.seg0 = (int)nseg;
+        nseg += T.nseg;
+    }
+    const bool sym = (size_t)sW * kUnitSources * 6 <= S->colpart_cap &&
+                     (size_t)nseg * S->sTM * 6 <= S->rowpart_cap;
+    int nt = 0;
+    long long W = 0;
+    if (!sym) {
+        for (int q = 0; q < n_sys; ++q) {
+            SJob* j = S->active[q];
+            const long long N = j->spec.n_points;
+            const int nu = (int)((N + kUnitSources - 1) / kUnitSources);
+            for (long long t = 0; t < N; t += S->TM) {
+                TileDesc& T = st.tiles[nt++];
+                T.sys = q;
+                T.t0 = (int)(j->pt_off + t);
+                T.tn = (int)std::min<long long>(S->TM, N - t);
+                T.s0 = (int)j->pt_off;
+                T.sn = (int)N;
+                T.nu = nu;
+                T.u0 = W;
+                W += nu;
+            }
+        }
+        if ((e = cudaMemcpyAsync(S->d_tiles, st.tiles, nt * sizeof(TileDesc), cudaMemcpyHostToDevice, s))) return e;
+    } else {
+        if ((e = cudaMemcpyAsync(S->d_stiles, st.stiles, snt * sizeof(SymTile), cudaMemcpyHostToDevice, s))) return e;
+    }
     if ((e = cudaMemcpyAsync(S->d_sc, st.sc, n_sys * sizeof(SysConst), cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaEventRecord(st.used, s))) return e;
-    MrsLaunch L;
-    L.tiles = S->d_tiles;
-    L.n_tiles = nt;
-    L.W = W;
-    L.P = (int)std::min<long long>(S->P, W);
-    L.sc = S->d_sc;
-    L.X = S->pX;
-    L.f = S->pf;
-    L.n = S->pn;
-    L.Xt = S->pX;
-    L.u = S->pu;
-    L.w = S->pw;
-    L.partial = S->d_partial;
-    L.counters = S->d_counters;
-    L.err = S->ctx->d_err;
-    if ((e = launch_mrs_f32(S->config, true, L, s))) return e;
+    if (sym) {
+        SymLaunch L;
+        L.tiles = S->d_stiles;
+        L.n_tiles = snt;
+        L.TM = S->sTM;
+        L.W = sW;
+        L.P = sP;
+        L.sc = S->d_sc;
+        L.X = S->pX;
+        L.f = S->pf;
+        L.n = S->pn;
+        L.u = S->pu;
+        L.w = S->pw;
+        L.rowpart = S->d_rowpart;
+        L.colpart = S->d_colpart;
+        L.err = S->ctx->d_err;
+        if ((e = launch_mrs_sym(S->sym_config, true, L, s))) return e;
+    } else {
+        MrsLaunch L;
+        L.tiles = S->d_tiles;
+        L.n_tiles = nt;
+        L.W = W;
+        L.P = (int)std::min<long long>(S->P, W);
+        L.sc = S->d_sc;
+        L.X = S->pX;
+        L.f = S->pf;
+        L.n = S->pn;
+        L.Xt = S->pX;
+        L.u = S->pu;
+        L.w = S->pw;
+        L.partial = S->d_partial;
+        L.counters = S->d_counters;
+        L.err = S->ctx->d_err;
+        if ((e = launch_mrs_f32(S->config, true, L, s))) return e;
+    }
     // stage updates and copy-out
     std::vector<SJob*> keep;
     for (SJob* j : S->active) {
@@ -382,6 +454,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
     S->active.swap(keep);
     std::lock_guard<std::mutex> g(S->mu);
     S->iterations += 1;
+    S->sym_iterations += sym ? 1 : 0;
     S->pairs += pairs;
     return cudaSuccess;
 }
@@ -477,8 +550,12 @@ void server_free(mrs_server* S)
     cudaFree(S->d_sc);
     cudaFree(S->d_partial);
     cudaFree(S->d_counters);
+    cudaFree(S->d_stiles);
+    cudaFree(S->d_rowpart);
+    cudaFree(S->d_colpart);
     for (auto& st : S->stage) {
         cudaFreeHost(st.tiles);
+        cudaFreeHost(st.stiles);
         cudaFreeHost(st.sc);
         if (st.used) cudaEventDestroy(st.used);
     }
@@ -503,10 +580,12 @@ int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int ma
     mrs_server* S = new mrs_server();
     S->ctx = ctx;
     S->max_slots = max_slots;
-    // pools: 30 % of the budget as point slots (5 float32 [.][3] arrays, 60 B per point),
-    // 70 % as bytes for rod state (~248 B per node)
-    const size_t pt_cap = (size_t)(0.30 * (double)hbm_budget_bytes) / 60;
+    // pools: 27 % of the budget as point slots (5 float32 [.][3] arrays, 60 B per point),
+    // 70 % as bytes for rod state (~248 B per node), 3 % (at most 3 GiB) as scratch of the
+    // symmetric launch (two thirds column partials, one third row partials)
+    const size_t pt_cap = (size_t)(0.27 * (double)hbm_budget_bytes) / 60;
     const size_t by_cap = (size_t)(0.70 * (double)hbm_budget_bytes) / kByteAlign;
+    const size_t sym_bytes = std::min<size_t>((size_t)(kServeSymShare * (double)hbm_budget_bytes), kServeSymMax);
     S->config = kServeConfig;
     S->TM = kConfigs[S->config].threads * kConfigs[S->config].tpt;
     int occ = 0, st;
@@ -516,6 +595,17 @@ int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int ma
         return MRS_ECUDA;
     }
     S->P = ctx->num_sms * occ;
+    S->sym_config = kServeSymConfig;
+    S->sTM = kConfigs[S->sym_config].threads * kConfigs[S->sym_config].tpt;
+    if (occupancy_sym(S->sym_config, true, &occ) != MRS_OK || occ < 1) {
+        delete S;
+        set_error("occupancy query failed");
+        return MRS_ECUDA;
+    }
+    S->sP = ctx->num_sms * occ;
+    S->colpart_cap = sym_bytes / 3 * 2 / sizeof(float);
+    S->rowpart_cap = sym_bytes / 3 / sizeof(float);
+    // tiles of the symmetric table (TM = sTM >= TM) never outnumber the ordered ones
     S->tile_cap = (int)std::min<size_t>(pt_cap / S->TM + max_slots + 1, (size_t)kMaxServeTiles);
     S->sys_cap = max_slots;
     if ((st = dalloc(&S->pX, 3 * pt_cap)) || (st = dalloc(&S->pf, 3 * pt_cap)) ||
@@ -523,7 +613,9 @@ int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int ma
         (st = dalloc(&S->pw, 3 * pt_cap)) || (st = dalloc(&S->d_bytes, by_cap * kByteAlign)) ||
         (st = dalloc(&S->d_tiles, (size_t)S->tile_cap)) || (st = dalloc(&S->d_sc, (size_t)S->sys_cap)) ||
         (st = dalloc(&S->d_partial, (size_t)2 * S->P * 12 * S->TM)) ||
-        (st = dalloc(&S->d_counters, (size_t)S->tile_cap))) {
+        (st = dalloc(&S->d_counters, (size_t)S->tile_cap)) ||
+        (st = dalloc(&S->d_stiles, (size_t)S->tile_cap)) ||
+        (st = dalloc(&S->d_rowpart, S->rowpart_cap)) || (st = dalloc(&S->d_colpart, S->colpart_cap))) {
         server_free(S);
         return st;
     }
@@ -532,6 +624,7 @@ int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int ma
     cudaError_t e = cudaMemset(S->d_counters, 0, sizeof(int) * (size_t)S->tile_cap);
     for (auto& sg : S->stage) {
         if (!e) e = cudaHostAlloc((void**)&sg.tiles, sizeof(TileDesc) * (size_t)S->tile_cap, cudaHostAllocDefault);
+        if (!e) e = cudaHostAlloc((void**)&sg.stiles, sizeof(SymTile) * (size_t)S->tile_cap, cudaHostAllocDefault);
         if (!e) e = cudaHostAlloc((void**)&sg.sc, sizeof(SysConst) * (size_t)S->sys_cap, cudaHostAllocDefault);
         if (!e) e = cudaEventCreateWithFlags(&sg.used, cudaEventDisableTiming);
         if (!e) e = cudaEventRecord(sg.used, 0);
@@ -669,7 +762,7 @@ int serve_drain(mrs_server* S, double timeout_s)
 }
 
 int serve_stats(mrs_server* S, int64_t* iterations, int64_t* completed, double* pairs,
-                int* peak_active, size_t* peak_pool_bytes)
+                int* peak_active, size_t* peak_pool_bytes, int64_t* symmetric_iterations)
 {
     clear_error();
     MRS_REQUIRE(S != nullptr, "NULL server");
@@ -679,6 +772,7 @@ int serve_stats(mrs_server* S, int64_t* iterations, int64_t* completed, double* 
     if (pairs) *pairs = S->pairs;
     if (peak_active) *peak_active = S->peak_active;
     if (peak_pool_bytes) *peak_pool_bytes = S->pts.peak() * 60 + S->bytes.peak() * kByteAlign;
+    if (symmetric_iterations) *symmetric_iterations = S->sym_iterations;
     return MRS_OK;
 }
 

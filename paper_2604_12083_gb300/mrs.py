@@ -141,7 +141,7 @@ def lib():
         L.serve_poll.argtypes = [_vp, ctypes.c_uint64, _ip, _dp]
         L.serve_drain.argtypes = [_vp, ctypes.c_double]
         L.serve_cancel.argtypes = [_vp, ctypes.c_uint64]
-        L.serve_stats.argtypes = [_vp, _i64p, _i64p, _dp, _ip, ctypes.POINTER(ctypes.c_size_t)]
+        L.serve_stats.argtypes = [_vp, _i64p, _i64p, _dp, _ip, ctypes.POINTER(ctypes.c_size_t), _i64p]
         L.serve_destroy.argtypes = [_vp]
         L.mrs_velocity_noalloc.argtypes = [ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                            ctypes.c_double, ctypes.c_double, _vp]
@@ -424,11 +424,13 @@ class Server:
 
     def stats(self):
         it, done, peak = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
-        pairs, pool = ctypes.c_double(), ctypes.c_size_t()
+        pairs, pool, sym = ctypes.c_double(), ctypes.c_size_t(), ctypes.c_int64()
         _check(lib().serve_stats(self.handle, ctypes.byref(it), ctypes.byref(done),
-                                 ctypes.byref(pairs), ctypes.byref(peak), ctypes.byref(pool)))
+                                 ctypes.byref(pairs), ctypes.byref(peak), ctypes.byref(pool),
+                                 ctypes.byref(sym)))
         return {"iterations": it.value, "completed": done.value, "pairs": pairs.value,
-                "peak_active": peak.value, "peak_pool_bytes": pool.value}
+                "peak_active": peak.value, "peak_pool_bytes": pool.value,
+                "symmetric_iterations": sym.value}
 
     def close(self):
         if self.handle:

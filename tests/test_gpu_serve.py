@@ -86,6 +86,9 @@ def test_results_same_alone_and_in_mix(ctx):
         srv.drain()
         st = srv.stats()
         assert st["peak_active"] >= 6
+        # with 1 GiB the scratch holds these iterations' partials: the batched launches ran
+        # the symmetric kernel (each unordered pair once)
+        assert st["symmetric_iterations"] >= 1
         assert rel(bv2[3].cpu().numpy(), u_alone) < TOL32 and rel(bv2[4].cpu().numpy(), w_alone) < TOL32
         assert rel(br2[0].cpu().numpy() - pr.X, X_alone - pr.X) < 1e-4
         # and the velocity job matches the FP64 oracle
@@ -105,14 +108,18 @@ def test_results_same_alone_and_in_mix(ctx):
 
 def test_admission_by_pool_budget(ctx):
     """A pool that holds only a few jobs at once: every job still completes, never more
-    admitted than fit."""
+    admitted than fit.  Its symmetric scratch (3 % of 4 MiB) is too small for these jobs'
+    partial sums, so every batched launch takes the ordered kernel; results match the oracle."""
     from paper_2604_12083_gb300 import mrs
-    srv = mrs.Server(ctx, 4 << 20, 64)    # 4 MiB: ~20k point slots
+    import oracle
+    oracle.build()
+    srv = mrs.Server(ctx, 4 << 20, 64)    # 4 MiB: ~18k point slots
     try:
         bufs = []
         tickets = []
+        jobs = [velocity_job(300 + i, 16) for i in range(16)]   # 4096 points each
         for i in range(16):
-            t, b = run_velocity(srv, velocity_job(300 + i, 16))   # 4096 points each
+            t, b = run_velocity(srv, jobs[i])
             tickets.append(t)
             bufs.append(b)
         srv.drain()
@@ -120,8 +127,12 @@ def test_admission_by_pool_budget(ctx):
         assert st["completed"] == 16
         assert st["peak_active"] <= 5
         assert st["peak_pool_bytes"] <= 4 << 20
+        assert st["symmetric_iterations"] == 0
         for b in bufs:
             assert torch.isfinite(b[3]).all() and torch.isfinite(b[4]).all()
+        p = jobs[3]
+        ur, wr = oracle.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+        assert rel(bufs[3][3].cpu().numpy(), ur) < TOL32 and rel(bufs[3][4].cpu().numpy(), wr) < TOL32
     finally:
         srv.close()
 
@@ -149,8 +160,16 @@ def test_cancel_waiting_job(ctx):
     from paper_2604_12083_gb300 import mrs
     srv = mrs.Server(ctx, 1 << 28, 1)
     try:
+        pw = velocity_job(501, 4)
         t_long, _ = run_rod(srv, rod_job(500, 4, M=256), nsteps=1500, scheme=0)
-        t_wait, bw = run_velocity(srv, velocity_job(501, 4))
+        # the scheduler thread admits the long job asynchronously: wait until it has run an
+        # iteration (1500 Euler steps take far longer than this wait)
+        import time
+        t0 = time.time()
+        while srv.stats()["iterations"] < 1 and time.time() - t0 < 10.0:
+            time.sleep(1e-4)
+        assert srv.stats()["iterations"] >= 1
+        t_wait, bw = run_velocity(srv, pw)
         srv.cancel(t_wait)
         with pytest.raises(mrs.MrsError) as e:
             srv.cancel(t_long)
