@@ -150,7 +150,7 @@ MRS_API int mrs_velocity_noalloc(int64_t n_points, const float* X, const float* 
 /* Explicit plans: build once, then execute many times (e.g. inside a CUDA graph).
  *   config  -1: the library's choice (tuned table or heuristic); otherwise an index into
  *           mrs_plan_config_count() kernel configurations (tile shape / targets per thread).
- *           Configurations 17..23 are symmetric: when the targets are the sources (Xt NULL
+ *           Configurations 17..26 are symmetric: when the targets are the sources (Xt NULL
  *           or equal to X) each unordered pair {i, j} is evaluated once and serves both points
  *           (the kernel values depend on |r| only and the reversed pair has separation -r),
  *           and execution launches the persistent pair kernel plus a small deterministic

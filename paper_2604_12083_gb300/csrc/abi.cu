@@ -64,7 +64,7 @@ int default_ordered_config(int n_sys, const int64_t* offsets)
 }
 
 // Symmetric configuration used by default, and the largest scratch it may take by default.
-constexpr int kDefaultSymConfig = 23;
+constexpr int kDefaultSymConfig = 25;
 constexpr double kSymScratchCap = 4.0 * 1024 * 1024 * 1024;
 
 // Work units and column-partial bytes of a symmetric plan with tiles of TM points.
@@ -134,7 +134,7 @@ static int sym_plan_build(mrs_plan* p, mrs_ctx* ctx, int cfg, const int64_t* off
         set_error("occupancy query failed for config %d", cfg);
         return MRS_ECUDA;
     }
-    long long P = (long long)ctx->num_sms * occ;
+    long long P = (long long)ctx->num_sms * occ * std::max(1, kc.over);
     if (P > W) P = W;
     long long nseg = 0;
     for (SymTile& T : tiles) {
@@ -280,7 +280,7 @@ int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, doubl
         set_error("occupancy query failed for config %d", p->ocfg);
         return MRS_ECUDA;
     }
-    long long P = (long long)ctx->num_sms * occ;
+    long long P = (long long)ctx->num_sms * occ * std::max(1, kc.over);
     if (P > W) P = W;
     p->P = (int)P;
     const size_t part_floats = (size_t)2 * P * 12 * p->TM;

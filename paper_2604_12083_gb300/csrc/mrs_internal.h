@@ -73,6 +73,8 @@ struct KernelConfig {
     int unroll;    // source-loop unroll of the packed loop (independent pair chains in flight)
     int sq;        // 1: s^2 = s*s by a packed multiply instead of an SFU reciprocal
     int sym;       // 1: each unordered pair once (targets = sources only; mrs_sym.cu)
+    int over;      // CTAs launched per resident CTA slot (0 or 1: one wave; > 1: the hardware
+                   // block scheduler hands the later CTAs to SMs as earlier ones finish)
 };
 
 // Configurations compiled into the library (index = plan config id).

@@ -437,6 +437,8 @@ const KernelConfig kConfigs[] = {
     // symmetric (mrs_sym.cu): packs of two points per thread, duplicated sources
     {128, 4, 1, 1, 0, 1}, {128, 4, 1, 1, 0, 1}, {128, 4, 1, 1, 1, 1}, {384, 4, 1, 1, 0, 1},
     {128, 6, 1, 1, 1, 1}, {128, 8, 1, 1, 1, 1}, {64, 6, 1, 1, 1, 1},
+    // ... the last three launched as 2, 4 and 8 waves of CTAs (KernelConfig::over)
+    {64, 6, 1, 1, 1, 1, 2}, {64, 6, 1, 1, 1, 1, 4}, {64, 6, 1, 1, 1, 1, 8},
 };
 const int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 

@@ -471,7 +471,8 @@ static int occ_sym_t(int* n)
 // Symmetric configurations (ids continue the ordered table of mrs_kernels.cu).  Measured on the
 // 32768-point system (ms per call, both kernels): 17: 1.80 (warp-shuffle reduction of each
 // source's share), 18: 1.68, 19: 1.67, 20: 1.68 (one 384-thread CTA per SM), 21: 1.653,
-// 22: 1.651, 23: 1.642 (the default).
+// 22: 1.651, 23: 1.630, and 23 launched as 2 / 4 / 8 waves of CTAs (24, 25, 26): 1.622, 1.610
+// (the default), 1.628.  On the 512-system batch 26 is the fastest (21.2 ms).
 #define MRS_SYM_DISPATCH(cfg, comp, FN, ...)                             \
     switch (cfg) {                                                       \
         MRS_SYM_CASE(17, 128, 4, false, false, FN, __VA_ARGS__)          \
@@ -481,6 +482,9 @@ static int occ_sym_t(int* n)
         MRS_SYM_CASE_X(21, 128, 6, true, true, 1, 2, FN, __VA_ARGS__)    \
         MRS_SYM_CASE_X(22, 128, 8, true, true, 1, 2, FN, __VA_ARGS__)    \
         MRS_SYM_CASE_X(23, 64, 6, true, true, 1, 4, FN, __VA_ARGS__)     \
+        MRS_SYM_CASE_X(24, 64, 6, true, true, 1, 4, FN, __VA_ARGS__)     \
+        MRS_SYM_CASE_X(25, 64, 6, true, true, 1, 4, FN, __VA_ARGS__)     \
+        MRS_SYM_CASE_X(26, 64, 6, true, true, 1, 4, FN, __VA_ARGS__)     \
     default: break;                                                      \
     }
 

@@ -89,7 +89,7 @@ class RangeAlloc {
 
 constexpr int kMaxRodsPerJob = 1024;
 constexpr int kServeConfig = 8;             // 64 threads x 4 targets, packed f32x2 (TM = 256)
-constexpr int kServeSymConfig = 23;         // symmetric, 64 threads x 6 points (TM = 384)
+constexpr int kServeSymConfig = 25;         // symmetric, 64 threads x 6 points (TM = 384), 4 waves
 constexpr double kServeSymShare = 0.03;     // share of the budget for symmetric scratch ...
 constexpr size_t kServeSymMax = (size_t)3 << 30;   // ... up to 3 GiB
 constexpr int kMaxServeTiles = 1 << 20;     // tiles of one iteration's batched launch
@@ -577,6 +577,10 @@ int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int ma
     MRS_REQUIRE(hbm_budget_bytes >= ((size_t)1 << 20), "hbm_budget_bytes must be at least 1 MiB");
     *srv = nullptr;
     MRS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    // point indices of the batched launch are 32-bit: the point pool (27 % of the budget at 60 B
+    // per point) must stay below 2^31 points
+    MRS_REQUIRE((double)hbm_budget_bytes * 0.27 / 60.0 < (double)((1u << 31) - (1u << 24)),
+                "hbm_budget_bytes too large (%zu)", hbm_budget_bytes);
     mrs_server* S = new mrs_server();
     S->ctx = ctx;
     S->max_slots = max_slots;
@@ -602,7 +606,7 @@ int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int ma
         set_error("occupancy query failed");
         return MRS_ECUDA;
     }
-    S->sP = ctx->num_sms * occ;
+    S->sP = ctx->num_sms * occ * std::max(1, kConfigs[S->sym_config].over);
     S->colpart_cap = sym_bytes / 3 * 2 / sizeof(float);
     S->rowpart_cap = sym_bytes / 3 / sizeof(float);
     // tiles of the symmetric table (TM = sTM >= TM) never outnumber the ordered ones
