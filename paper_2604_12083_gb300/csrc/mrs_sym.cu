@@ -440,11 +440,11 @@ static cudaError_t sym_prepare()
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// The dynamic shared-memory limit above 48 KB is raised by occupancy_sym, which every plan and
+// server calls when it is built, so a launch makes no attribute call (stream capture safe).
 template <int BLOCK, int TPT, bool COMP, bool SQ, bool SKEW, int UNR, int MINB>
 static cudaError_t launch_sym_t(const SymLaunch& L, cudaStream_t s)
 {
-    cudaError_t e0 = sym_prepare<BLOCK, TPT, COMP, SQ, SKEW, UNR, MINB>();
-    if (e0 != cudaSuccess) return e0;
     mrs_f32_sym<BLOCK, TPT, COMP, SQ, SKEW, UNR, MINB>
         <<<L.P, BLOCK, sym_smem_bytes<BLOCK, TPT, COMP>(), s>>>(L);
     cudaError_t e = cudaGetLastError();

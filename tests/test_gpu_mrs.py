@@ -303,3 +303,37 @@ def test_large_ragged_single_system_sampled(ctx, orc, config):
     idx = np.concatenate([rng.choice(N, 250, replace=False), np.arange(N - 6, N)])
     ur, wr = orc.mrs_velocity(p.X, p.f, p.n, 0.02, 1.0, xt=p.X[idx])
     assert rel_l2(u[idx], ur) < TOL32 and rel_l2(w[idx], wr) < TOL32
+
+
+@pytest.mark.parametrize("config", [8, 25, 26])
+def test_plan_replays_in_cuda_graph(ctx, orc, config):
+    """A plan's execution (one persistent launch, plus the reduction kernel for symmetric
+    configurations) captured in a CUDA graph and replayed gives the eager result bit for bit,
+    and the oracle's on a ragged batch; replays after the inputs change pick up the new inputs."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.batch_systems(seed=70, n_sys=12, lo_exp=8, hi_exp=13)
+    X, f, n = dev(p.X), dev(p.f), dev(p.n)
+    pl = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32_COMP,
+                  config=config)
+    ue, we = torch.empty_like(X), torch.empty_like(X)
+    pl.execute(X, f, n, ue, we)
+    torch.cuda.synchronize()
+    u, w = torch.full_like(X, float("nan")), torch.full_like(X, float("nan"))
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            pl.execute(X, f, n, u, w, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(u, ue) and torch.equal(w, we)
+    ur, wr = orc.mrs_velocity_batch(p.offsets, p.X, p.f, p.n, 0.0, p.mu, eps_per_sys=p.eps)
+    assert rel_l2(u.cpu().numpy(), ur) < TOL32 and rel_l2(w.cpu().numpy(), wr) < TOL32
+    f.mul_(-2.0)                      # linear in the forces and torques
+    n.mul_(-2.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert rel_l2(u.cpu().numpy(), -2.0 * ur) < TOL32 and rel_l2(w.cpu().numpy(), -2.0 * wr) < TOL32
+    pl.close()
