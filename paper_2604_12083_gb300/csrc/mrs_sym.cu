@@ -472,7 +472,9 @@ static int occ_sym_t(int* n)
 // 32768-point system (ms per call, both kernels): 17: 1.80 (warp-shuffle reduction of each
 // source's share), 18: 1.68, 19: 1.67, 20: 1.68 (one 384-thread CTA per SM), 21: 1.653,
 // 22: 1.651, 23: 1.630, and 23 launched as 2 / 4 / 8 waves of CTAs (24, 25, 26): 1.622, 1.610
-// (the default), 1.628.  On the 512-system batch 26 is the fastest (21.2 ms).
+// (the default), 1.628.  On the 512-system batch 26 is the fastest (21.2 ms).  Computing the next
+// source's kernel values while accumulating the current one's (software pipelining, 2 packs,
+// 200 registers) was slower: 1.74 ms.
 #define MRS_SYM_DISPATCH(cfg, comp, FN, ...)                             \
     switch (cfg) {                                                       \
         MRS_SYM_CASE(17, 128, 4, false, false, FN, __VA_ARGS__)          \
