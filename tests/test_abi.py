@@ -56,3 +56,16 @@ def test_errors_without_gpu_are_reported_not_fatal(libpath):
     st = mrs.lib().mrs_ctx_create(ctypes.byref(h), 0)
     assert st in (mrs.MRS_EINVAL, mrs.MRS_ECUDA)
     assert len(mrs.lib().mrs_last_error()) > 0
+
+
+def test_config_table_host_queries(libpath):
+    """The configuration table answers without a device: ordered configurations first, then
+    the symmetric ones (each unordered pair evaluated once); out-of-range ids are rejected."""
+    from paper_2604_12083_gb300 import mrs
+    n = mrs.plan_config_count()
+    flags = [mrs.plan_config_symmetric(c) for c in range(n)]
+    assert not any(flags[:17]) and all(flags[17:]) and len(flags) > 17
+    assert mrs.lib().mrs_plan_config_symmetric(n) == -1
+    assert mrs.lib().mrs_plan_config_symmetric(-1) == -1
+    with pytest.raises(mrs.MrsError):
+        mrs.plan_config_symmetric(n)
