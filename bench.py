@@ -566,8 +566,21 @@ def run_ours(args, world, rank, local, pg):
     w = torch.empty_like(X)
     eps = float(p.eps[0])
 
+    # the public call (plan cached in the context, the library's choice of configuration), or
+    # with --config an explicit plan of that configuration
+    forced = None
+    if args.config >= 0:
+        forced = mrs.Plan(ctx, p.offsets, p.mu, eps, precision=mrs.MRS_F32_COMP, config=args.config)
+
+    def velocity(Xa, fa, na, ua, wa, s=None):
+        if forced is not None:
+            forced.execute(Xa, fa, na, ua, wa, stream=s)
+        else:
+            mrs.mrs_velocity(ctx, p.offsets, Xa, fa, na, ua, wa, p.mu, eps,
+                             precision=mrs.MRS_F32_COMP, stream=s)
+
     def step():
-        mrs.mrs_velocity(ctx, p.offsets, X, f, n, u, w, p.mu, eps, precision=mrs.MRS_F32_COMP)
+        velocity(X, f, n, u, w)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MiB > L2
     for _ in range(max(3, args.warmup)):
@@ -575,9 +588,12 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
     # the configuration mrs_velocity chose for this shape (the same library choice as a plan
     # built with config = -1): symmetric ones launch the pair kernel and a reduction kernel
-    probe = mrs.Plan(ctx, p.offsets, p.mu, eps, precision=mrs.MRS_F32_COMP)
-    plan_info = probe.info()
-    probe.close()
+    if forced is not None:
+        plan_info = forced.info()
+    else:
+        probe = mrs.Plan(ctx, p.offsets, p.mu, eps, precision=mrs.MRS_F32_COMP)
+        plan_info = probe.info()
+        probe.close()
     sym = mrs.plan_config_symmetric(plan_info["config"])
     launches_per_step = 2 if sym else 1
     kernel_name = ("mrs_f32_sym + mrs_sym_reduce (whole step)" if sym else "mrs_f32_persistent")
@@ -644,8 +660,7 @@ def run_ours(args, world, rank, local, pg):
             stream.wait_event(h2d_done[k])
             stream.wait_event(d2h_done[k])   # the result of step i-2 has been read
             bX, bf, bn, bu, bw = bufs[k]
-            mrs.mrs_velocity(ctx, p.offsets, bX, bf, bn, bu, bw, p.mu, eps,
-                             precision=mrs.MRS_F32_COMP, stream=stream)
+            velocity(bX, bf, bn, bu, bw, s=stream)
             comp_done[k].record(stream)
             if i + 1 < n_steps:
                 h2d((i + 1) % 2)
@@ -725,6 +740,8 @@ def run_ours(args, world, rank, local, pg):
                                         "100-step rod integrations, N log-uniform [1k, 64k]")
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if forced is not None:
+        forced.close()
     ctx.close()
 
 
@@ -736,6 +753,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--config", type=int, default=-1,
+                    help="force this pair-sum plan configuration (default: the library's choice)")
     ap.add_argument("--case", choices=["main", "rod_kernels"], default="main",
                     help="rod_kernels: time the rod force and update kernels on 1M nodes")
     args = ap.parse_args()

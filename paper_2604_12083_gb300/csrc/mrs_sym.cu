@@ -474,7 +474,9 @@ static int occ_sym_t(int* n)
 // 22: 1.651, 23: 1.630, and 23 launched as 2 / 4 / 8 waves of CTAs (24, 25, 26): 1.622, 1.610
 // (the default), 1.628.  On the 512-system batch 26 is the fastest (21.2 ms).  Computing the next
 // source's kernel values while accumulating the current one's (software pipelining, 2 packs,
-// 200 registers) was slower: 1.74 ms; unrolling 25's source loop twice changed nothing (1.612).
+// 200 registers) was slower: 1.74 ms; unrolling 25's source loop twice changed nothing (1.612);
+// keeping the tile's f and n in shared memory (126 registers, 16 warps per SM, 64-source
+// chunks) was slower too: 1.68 ms at 4 points per thread, 1.64 ms at 6.
 #define MRS_SYM_DISPATCH(cfg, comp, FN, ...)                             \
     switch (cfg) {                                                       \
         MRS_SYM_CASE(17, 128, 4, false, false, FN, __VA_ARGS__)          \
