@@ -337,3 +337,22 @@ def test_plan_replays_in_cuda_graph(ctx, orc, config):
     torch.cuda.synchronize()
     assert rel_l2(u.cpu().numpy(), -2.0 * ur) < TOL32 and rel_l2(w.cpu().numpy(), -2.0 * wr) < TOL32
     pl.close()
+
+
+def test_nonfinite_inputs_raise_the_flag_through_the_symmetric_path(ctx):
+    """A NaN torque in a symmetric plan's system spreads to every point through the column
+    partials; the reduction kernel raises the device flag once."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.single_system(seed=71, n_fil=3, M=700)
+    X, f, n = dev(p.X), dev(p.f), dev(p.n)
+    u, w = torch.empty_like(X), torch.empty_like(X)
+    pl = mrs.Plan(ctx, p.offsets, p.mu, float(p.eps[0]), precision=mrs.MRS_F32_COMP, config=25)
+    assert ctx.device_status() == 0
+    pl.execute(X, f, n, u, w)
+    assert ctx.device_status() == 0
+    n[1500, 2] = float("nan")
+    pl.execute(X, f, n, u, w)
+    assert ctx.device_status() & mrs.MRS_FLAG_NONFINITE
+    assert ctx.device_status() == 0
+    assert not torch.isfinite(u).all()
+    pl.close()
