@@ -14,7 +14,10 @@
 // of iteration k+1 never overwrite rows that sweep k still reads.
 // The host enqueues sweep k, then (speculatively) the fine solves of iteration k+1, and only
 // then reads eta~^k; if iteration k converged, the speculative fine work is discarded (it only
-// writes the fine buffers).  No kernel waits on another kernel.
+// writes the fine buffers).  Speculation is skipped when the increments so far predict that
+// iteration k converges (eta~^{k-1} * (eta~^{k-1} / eta~^{k-2}) < tol, i.e. the geometric
+// trend of the last two increments): the host then reads eta~^k first and enqueues the fine
+// solves of iteration k+1 only if they are needed.  No kernel waits on another kernel.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -208,7 +211,14 @@ extern "C" int parareal_run_pipelined(mrs_ctx* ctx, int n_rods, const int64_t* r
     std::memset(&stats, 0, sizeof(stats));
     double last = INFINITY;
     int status = MRS_OK;
+    bool fine_queued = true;   // the fine solves of the next iteration are enqueued
     for (int k = 1; k <= max_iter && k <= Ns; ++k) {
+        if (!fine_queued) {    // not speculated: enqueue them now (U^{k-1} is final)
+            if ((st = enqueue_fine(k))) return st;
+            for (int j = 0; j < n_groups; ++j)
+                if (std::max(g_lo(j), k) <= g_hi(j)) MRS_CHECK_CUDA(cudaStreamWaitEvent(sC, copied[j], 0));
+            fine_queued = true;
+        }
         // the correction sweep of iteration k (Eq. serial_correct) on the sweep stream
         double* inc = INC.p + (k - 1);
         const double* FX = FXb[k % 2].p;
@@ -233,10 +243,17 @@ extern "C" int parareal_run_pipelined(mrs_ctx* ctx, int n_rods, const int64_t* r
         MRS_CHECK_CUDA(cudaEventRecord(end_ev, sC));
         // speculative: the next iteration's fine solves start as the sweep publishes states.
         // The next sweep overwrites U[n] only after the group reading U[n] has copied it.
-        if (k < max_iter && k < Ns) {
+        fine_queued = false;
+        bool speculate = k < max_iter && k < Ns;
+        if (speculate && tol > 0.0 && k >= 3) {
+            const double a = stats.incr[k - 2], b = stats.incr[k - 3];   // eta~^{k-1}, eta~^{k-2}
+            if (b > 0.0 && a < b && a * (a / b) < tol) speculate = false;
+        }
+        if (speculate) {
             if ((st = enqueue_fine(k + 1))) return st;
             for (int j = 0; j < n_groups; ++j)
                 if (std::max(g_lo(j), k + 1) <= g_hi(j)) MRS_CHECK_CUDA(cudaStreamWaitEvent(sC, copied[j], 0));
+            fine_queued = true;
         }
         MRS_CHECK_CUDA(cudaEventSynchronize(end_ev));
         const double incr = h_inc[k - 1];
