@@ -390,6 +390,8 @@ def extra_parareal(ctx, dev):
         small["runs"].append({"schedule": "pipelined (groups of 8)" if gs else "regular",
                               "iterations": st.iterations, "seconds": st.seconds,
                               "converged": ok, "final_increment": st.final_incr,
+                              "increments": [st.incr[i] for i in range(st.iterations)],
+                              "fine_steps_executed": st.fine_steps,
                               "speedup_vs_serial_fine": t_serial1 / st.seconds if ok else None,
                               "rel_diff_vs_serial_displacement":
                                   float(np.linalg.norm(dp - ds_) / np.linalg.norm(ds_))})

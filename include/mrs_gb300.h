@@ -85,6 +85,16 @@ MRS_API int mrs_ctx_destroy(mrs_ctx* ctx);
 /* Number of SMs of the context's device (host-side query; no GPU work). */
 MRS_API int mrs_ctx_num_sms(const mrs_ctx* ctx);
 
+/* Rod stepping path of the context (rod_step, parareal_run, parareal_run_pipelined).  With
+ * enable = 1 (the default) a batch of small instances -- at most ~650 nodes each (the state
+ * must fit shared memory), float32 pair sum, no Lennard-Jones term -- advances through all its
+ * steps in ONE launch: one CTA per instance keeps the instance's state in shared memory and runs
+ * forces, pair sum and update of every stage back to back.  With enable = 0, or for larger or
+ * Lennard-Jones instances, every step is forces -> pair-sum plan -> update kernels replayed from
+ * captured CUDA graphs.  Both compute the same steps; results agree to float32 rounding of the
+ * pair sum.  Host only.  Errors: MRS_EINVAL. */
+MRS_API int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable);
+
 /* Device-side anomaly flags raised by the pair-sum kernels of this context since the last call
  * (MRS_FLAG_NONFINITE: a non-finite u or omega was written, e.g. from non-finite inputs).
  * Synchronizes the device, returns the flags in *flags and clears them. */
@@ -289,9 +299,10 @@ MRS_API int parareal_run(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const
  * produced their input states (the sweep streams its results downstream), overlapping the
  * serial coarse/correction sweep with fine work.  The next iteration's fine solves are queued
  * before the current increment is known; if the current iteration converges, that work is
- * discarded.  From the third iteration on, when the last two increments extrapolate
- * geometrically below tol, the current increment is read first and the next fine solves are
- * queued only if needed.  All ordering is by CUDA events between streams (no device-side
+ * discarded.  When the fine solves of all slices fill the GPU (n_points x n_slices >= 65536)
+ * and, from the third iteration on, the last two increments extrapolate geometrically below
+ * tol, the current increment is read first and the next fine solves are queued only if
+ * needed.  All ordering is by CUDA events between streams (no device-side
  * waiting).
  * Arguments, outputs and errors as for parareal_run; group_size in 1..n_slices. */
 MRS_API int parareal_run_pipelined(mrs_ctx* ctx, int n_rods, const int64_t* rod_off,

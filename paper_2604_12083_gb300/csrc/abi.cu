@@ -449,6 +449,15 @@ int mrs_ctx_destroy(mrs_ctx* ctx)
 
 int mrs_ctx_num_sms(const mrs_ctx* ctx) { return ctx ? ctx->num_sms : 0; }
 
+int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable)
+{
+    clear_error();
+    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+    MRS_REQUIRE(enable == 0 || enable == 1, "enable must be 0 or 1");
+    ctx->fused_steps = enable != 0;
+    return MRS_OK;
+}
+
 int mrs_device_status(mrs_ctx* ctx, unsigned int* flags)
 {
     clear_error();

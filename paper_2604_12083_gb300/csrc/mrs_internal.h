@@ -250,6 +250,8 @@ struct mrs_ctx {
     size_t rod_ws_max = 256;
     // measured best kernel configurations (mrs_autotune)
     std::vector<mrs::TuneEntry> tuned;
+    // rod stepping of small systems in one fused launch per call (mrs_ctx_set_fused_steps)
+    bool fused_steps = true;
 };
 
 namespace mrs {

@@ -14,10 +14,14 @@
 // of iteration k+1 never overwrite rows that sweep k still reads.
 // The host enqueues sweep k, then (speculatively) the fine solves of iteration k+1, and only
 // then reads eta~^k; if iteration k converged, the speculative fine work is discarded (it only
-// writes the fine buffers).  Speculation is skipped when the increments so far predict that
-// iteration k converges (eta~^{k-1} * (eta~^{k-1} / eta~^{k-2}) < tol, i.e. the geometric
-// trend of the last two increments): the host then reads eta~^k first and enqueues the fine
-// solves of iteration k+1 only if they are needed.  No kernel waits on another kernel.
+// writes the fine buffers).  When the fine solves of all slices fill the GPU (at least
+// kSpecPoints points per batched stage), discarded speculative work costs real time, so
+// speculation is skipped when the increments so far predict that iteration k converges
+// (eta~^{k-1} * (eta~^{k-1} / eta~^{k-2}) < tol, the geometric trend of the last two
+// increments): the host then reads eta~^k first and enqueues the fine solves of iteration k+1
+// only if they are needed.  Smaller systems always speculate: their fine stages leave most of
+// the GPU idle, and a wrong prediction (e.g. increments that level off at the float32 floor of
+// the pair sum) would cost the overlap.  No kernel waits on another kernel.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -28,6 +32,8 @@
 using namespace mrs;
 
 namespace {
+
+constexpr double kSpecPoints = 65536.0;   // points per batched fine stage that fill the GPU
 
 struct DBuf {
     double* p = nullptr;
@@ -245,7 +251,7 @@ extern "C" int parareal_run_pipelined(mrs_ctx* ctx, int n_rods, const int64_t* r
         // The next sweep overwrites U[n] only after the group reading U[n] has copied it.
         fine_queued = false;
         bool speculate = k < max_iter && k < Ns;
-        if (speculate && tol > 0.0 && k >= 3) {
+        if (speculate && tol > 0.0 && k >= 3 && (double)N1 * Ns >= kSpecPoints) {
             const double a = stats.incr[k - 2], b = stats.incr[k - 3];   // eta~^{k-1}, eta~^{k-2}
             if (b > 0.0 && a < b && a * (a / b) < tol) speculate = false;
         }

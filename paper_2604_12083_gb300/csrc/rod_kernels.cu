@@ -96,17 +96,14 @@ __global__ void rot_sqrt_batch_kernel(int n, const double* R, double* S)
     if (i < n) rot_sqrt_dev(R + 9 * (size_t)i, S + 9 * (size_t)i);
 }
 
-// Segment k+1/2 (index idx within a rod of M nodes): internal force F and moment N in lab
-// coordinates (Eqs. mid_triad, F_comp_discrete, N_comp_discrete; Omega of Section IV-A at the
-// segment midpoint), written to o[0..5].
-__device__ void segment_fn(const RodLaunch& L, const double* __restrict__ X,
-                           const double* __restrict__ D, double t_off, long long k, int idx, int M,
-                           double* o)
+// Segment k+1/2 (index idx within a rod of M nodes; Xk, Dk point at node k, node k+1 follows)
+// at time t: internal force F and moment N in lab coordinates (Eqs. mid_triad,
+// F_comp_discrete, N_comp_discrete; Omega of Section IV-A at the segment midpoint), written to
+// o[0..5].
+__device__ __forceinline__ void segment_core(const mrs_rod_params& P, const double* Xk,
+                                             const double* Dk, double t, int idx, int M, double* o)
 {
-    const double ds = L.p.L / (double)(M - 1);
-    const int inst = (int)(k / L.nodes_per_inst);
-    const double t = L.t0[inst] + (double)(*L.step) * L.dt + t_off;
-    const double* Dk = D + 9 * (size_t)k;
+    const double ds = P.L / (double)(M - 1);
     const double* Dk1 = Dk + 9;
     double A[9], S[9], Dh[9];
 #pragma unroll
@@ -120,19 +117,18 @@ __device__ void segment_fn(const RodLaunch& L, const double* __restrict__ X,
 #pragma unroll
         for (int r = 0; r < 3; ++r)
             Dh[3 * i + r] = S[3 * r] * Dk[3 * i] + S[3 * r + 1] * Dk[3 * i + 1] + S[3 * r + 2] * Dk[3 * i + 2];
-    const double* Xk = X + 3 * (size_t)k;
     const double ids = 1.0 / ds;   // one division; float64 divisions are expensive here
     const double e[3] = {(Xk[3] - Xk[0]) * ids, (Xk[4] - Xk[1]) * ids, (Xk[5] - Xk[2]) * ids};
     const double s_mid = ((double)idx + 0.5) * ds;
-    const double om2 = -L.p.wave_k * L.p.wave_k * L.p.wave_A * sin(L.p.wave_k * s_mid + L.p.wave_f * t);
+    const double om2 = -P.wave_k * P.wave_k * P.wave_A * sin(P.wave_k * s_mid + P.wave_f * t);
     double F[3] = {0, 0, 0}, Nm[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const double Fi = L.p.b[i] * (dot3(e, Dh + 3 * i) - (i == 2 ? 1.0 : 0.0));
+        const double Fi = P.b[i] * (dot3(e, Dh + 3 * i) - (i == 2 ? 1.0 : 0.0));
         const int j = (i + 1) % 3, l = (i + 2) % 3;
         const double dD[3] = {(Dk1[3 * j] - Dk[3 * j]) * ids, (Dk1[3 * j + 1] - Dk[3 * j + 1]) * ids,
                               (Dk1[3 * j + 2] - Dk[3 * j + 2]) * ids};
-        const double Ni = L.p.a[i] * (dot3(dD, Dh + 3 * l) - (i == 1 ? om2 : 0.0));
+        const double Ni = P.a[i] * (dot3(dD, Dh + 3 * l) - (i == 1 ? om2 : 0.0));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             F[c] += Fi * Dh[3 * i + c];
@@ -145,6 +141,16 @@ __device__ void segment_fn(const RodLaunch& L, const double* __restrict__ X,
     o[3] = Nm[0];
     o[4] = Nm[1];
     o[5] = Nm[2];
+}
+
+// Segment k+1/2 of the batch at the current step's time (+ t_off).
+__device__ void segment_fn(const RodLaunch& L, const double* __restrict__ X,
+                           const double* __restrict__ D, double t_off, long long k, int idx, int M,
+                           double* o)
+{
+    const int inst = (int)(k / L.nodes_per_inst);
+    const double t = L.t0[inst] + (double)(*L.step) * L.dt + t_off;
+    segment_core(L.p, X + 3 * (size_t)k, D + 9 * (size_t)k, t, idx, M, o);
 }
 
 __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__ X,
@@ -293,6 +299,203 @@ __global__ void rod_update_kernel(const RodLaunch L, const double* X0, const dou
     for (int c = 0; c < 3; ++c) X1[3 * (size_t)k + c] = X0[3 * (size_t)k + c] + (double)u[3 * (size_t)k + c] * h;
 #pragma unroll
     for (int q = 0; q < 9; ++q) D1[9 * (size_t)k + q] = Dn[q];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fused fine propagator for small systems: one CTA advances one instance (a Parareal slice, or
+// the single system of a rod_step call) through all its time steps inside one launch.  The
+// instance's whole state lives in shared memory -- X, D, the RK2 midpoint state, the segment
+// forces, the float32 packs of positions, forces and torques, and the velocities -- and every
+// stage runs the same arithmetic as the batched kernels: segment_core (rotation square root,
+// internal force and moment), node_fn (node force and torque, float32 packs), the regularized
+// Stokeslet pair sum over the instance's points (float32, per-target accumulation in 32-source
+// chunks folded into Kahan pairs; the kernels written with d s^2 = 1 as in mrs_kernels.cu) and
+// rodrigues (Eqs. newx, newD).  Only __syncthreads separates the phases: no launches per step.
+// ---------------------------------------------------------------------------------------------
+struct FusedConst {   // pair-sum constants of the instance's system (see SysConst)
+    float e2, c1, c2, c3, c5, scale;
+};
+
+__device__ __forceinline__ float fused_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void fused_kahan(float& sum, float& comp, float v)
+{
+    const float y = __fsub_rn(v, comp);
+    const float t = __fadd_rn(sum, y);
+    comp = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
+// Velocities (u, w) of the instance's points for the state (sXs, sDs) at time t.
+template <int BLOCK>
+__device__ void fused_velocity(const mrs_rod_params& P, const FusedConst& K, int N1,
+                               const int2* sni, const double* sXs, const double* sDs, double t,
+                               double* sFN, float* sXf, float* sgf, float* smf, float* su, float* sw)
+{
+    const int tid = threadIdx.x;
+    for (int k = tid; k < N1; k += BLOCK) {
+        const int2 ni = sni[k];
+        if (ni.x < ni.y - 1) segment_core(P, sXs + 3 * k, sDs + 9 * k, t, ni.x, ni.y, sFN + 6 * k);
+    }
+    __syncthreads();
+    for (int k = tid; k < N1; k += BLOCK) {
+        const int2 ni = sni[k];
+        node_fn(sXs, k, ni.x < ni.y - 1 ? sFN + 6 * k : nullptr, ni.x > 0 ? sFN + 6 * (k - 1) : nullptr,
+                nullptr, nullptr, sXf, sgf, smf);
+    }
+    __syncthreads();
+    for (int i = tid; i < N1; i += BLOCK) {
+        const float xi = sXf[3 * i], yi = sXf[3 * i + 1], zi = sXf[3 * i + 2];
+        float sum[6], cmp[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            sum[q] = 0.f;
+            cmp[q] = 0.f;
+        }
+        for (int j0 = 0; j0 < N1; j0 += 32) {
+            const int j1 = min(N1, j0 + 32);
+            float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int j = j0; j < j1; ++j) {
+                const float rx = xi - sXf[3 * j], ry = yi - sXf[3 * j + 1], rz = zi - sXf[3 * j + 2];
+                const float fx = sgf[3 * j], fy = sgf[3 * j + 1], fz = sgf[3 * j + 2];
+                const float nx = smf[3 * j], ny = smf[3 * j + 1], nz = smf[3 * j + 2];
+                const float d = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, K.e2)));
+                const float s1 = fused_rsqrt(d);
+                const float s2 = s1 * s1;
+                const float s3 = s1 * s2, s5 = s3 * s2;
+                const float h1 = fmaf(K.e2, s3, s1);
+                const float h3 = fmaf(K.c1, s5, s3);
+                const float h4 = s3 * fmaf(s2, fmaf(K.c2, s2, K.c3), -0.5f);
+                const float h5 = s5 * fmaf(K.c5, s2, 1.5f);
+                const float bf = s3 * fmaf(fx, rx, fmaf(fy, ry, fz * rz));
+                const float bn = h5 * fmaf(nx, rx, fmaf(ny, ry, nz * rz));
+                const float hx = h3 * rx, hy = h3 * ry, hz = h3 * rz;
+                // u += H1 f + H2 (f.r) r + H3 (n x r);  w += H3 (f x r) + H4 n + H5 (n.r) r
+                acc[0] += h1 * fx + bf * rx + (ny * hz - nz * hy);
+                acc[1] += h1 * fy + bf * ry + (nz * hx - nx * hz);
+                acc[2] += h1 * fz + bf * rz + (nx * hy - ny * hx);
+                acc[3] += h4 * nx + bn * rx + (fy * hz - fz * hy);
+                acc[4] += h4 * ny + bn * ry + (fz * hx - fx * hz);
+                acc[5] += h4 * nz + bn * rz + (fx * hy - fy * hx);
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) fused_kahan(sum[q], cmp[q], acc[q]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            su[3 * i + c] = __fsub_rn(sum[c], cmp[c]) * K.scale;
+            sw[3 * i + c] = __fsub_rn(sum[3 + c], cmp[3 + c]) * K.scale;
+        }
+    }
+    __syncthreads();
+}
+
+// (X1, D1) = (X0 + u h, Rodrigues(D0, w, h)) for the instance's points; X1/D1 may alias X0/D0.
+template <int BLOCK>
+__device__ void fused_update(int N1, const double* sX0, const double* sD0, const float* su,
+                             const float* sw, double h, double* sX1, double* sD1)
+{
+    for (int k = threadIdx.x; k < N1; k += BLOCK) {
+        double Dl[9], Dn[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Dl[q] = sD0[9 * k + q];
+        rodrigues(Dl, (double)sw[3 * k], (double)sw[3 * k + 1], (double)sw[3 * k + 2], h, Dn);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sX1[3 * k + c] = sX0[3 * k + c] + (double)su[3 * k + c] * h;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) sD1[9 * k + q] = Dn[q];
+    }
+    __syncthreads();
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) rod_fine_fused_kernel(const RodLaunch L, double* X,
+                                                                double* D, int nsteps, int scheme,
+                                                                const FusedConst K)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int N1 = L.nodes_per_inst;
+    const int inst = blockIdx.x;
+    double* sX = reinterpret_cast<double*>(fsm);
+    double* sD = sX + 3 * N1;
+    double* sXh = sD + 9 * N1;
+    double* sDh = sXh + 3 * N1;
+    double* sFN = sDh + 9 * N1;
+    int2* sni = reinterpret_cast<int2*>(sFN + 6 * N1);
+    float* sXf = reinterpret_cast<float*>(sni + N1);
+    float* sgf = sXf + 3 * N1;
+    float* smf = sgf + 3 * N1;
+    float* su = smf + 3 * N1;
+    float* sw = su + 3 * N1;
+    double* gX = X + (size_t)inst * 3 * N1;
+    double* gD = D + (size_t)inst * 9 * N1;
+    for (int q = threadIdx.x; q < 3 * N1; q += BLOCK) sX[q] = gX[q];
+    for (int q = threadIdx.x; q < 9 * N1; q += BLOCK) sD[q] = gD[q];
+    for (int k = threadIdx.x; k < N1; k += BLOCK) sni[k] = L.node_info[k];
+    const double t0 = L.t0[inst] + (double)(*L.step) * L.dt;
+    __syncthreads();
+    for (int st = 0; st < nsteps; ++st) {
+        const double t = t0 + (double)st * L.dt;
+        fused_velocity<BLOCK>(L.p, K, N1, sni, sX, sD, t, sFN, sXf, sgf, smf, su, sw);
+        if (scheme == MRS_EULER) {
+            fused_update<BLOCK>(N1, sX, sD, su, sw, L.dt, sX, sD);
+        } else {
+            fused_update<BLOCK>(N1, sX, sD, su, sw, 0.5 * L.dt, sXh, sDh);
+            fused_velocity<BLOCK>(L.p, K, N1, sni, sXh, sDh, t + 0.5 * L.dt, sFN, sXf, sgf, smf, su, sw);
+            fused_update<BLOCK>(N1, sX, sD, su, sw, L.dt, sX, sD);
+        }
+    }
+    for (int q = threadIdx.x; q < 3 * N1; q += BLOCK) gX[q] = sX[q];
+    for (int q = threadIdx.x; q < 9 * N1; q += BLOCK) gD[q] = sD[q];
+}
+
+__global__ void rod_bump_step_kernel(long long* step, int nsteps) { *step += nsteps; }
+
+constexpr int kFusedBlock = 256;
+
+size_t fused_smem_bytes(int N1) { return (size_t)N1 * (30 * sizeof(double) + sizeof(int2) + 15 * sizeof(float)); }
+
+bool fused_fits(int N1)
+{
+    return N1 >= 2 && fused_smem_bytes(N1) <= kFusedMaxSmem;
+}
+
+cudaError_t launch_rod_fine_fused(const RodLaunch& L, double* X, double* D, int nsteps, int scheme,
+                                  double mu, double eps, cudaStream_t s)
+{
+    const int N1 = L.nodes_per_inst;
+    const int n_inst = L.N / N1;
+    if (L.N == 0 || nsteps <= 0) return cudaSuccess;
+    const size_t bytes = fused_smem_bytes(N1);
+    // raise the kernel's dynamic shared-memory limit once per device (not per launch)
+    static bool raised[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!raised[dev]) {
+        e = cudaFuncSetAttribute(rod_fine_fused_kernel<kFusedBlock>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedMaxSmem);
+        if (e != cudaSuccess) return e;
+        raised[dev] = true;
+    }
+    FusedConst K;
+    const double e2 = eps * eps;
+    K.e2 = (float)e2;
+    K.c1 = (float)(1.5 * e2);
+    K.c2 = (float)(3.75 * e2 * e2);
+    K.c3 = (float)(-0.75 * e2);
+    K.c5 = (float)(3.75 * e2);
+    K.scale = (float)(1.0 / (8.0 * M_PI * mu));
+    rod_fine_fused_kernel<kFusedBlock><<<n_inst, kFusedBlock, bytes, s>>>(L, X, D, nsteps, scheme, K);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    rod_bump_step_kernel<<<1, 1, 0, s>>>(L.step, nsteps);
+    return cudaGetLastError();
 }
 
 // Start times of the instances of a batch, t0[i] = t_first + i * dT, and the step counter reset:

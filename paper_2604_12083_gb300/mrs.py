@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "MRS_OK", 1: "MRS_EINVAL", 2: "MRS_ENOMEM", 3: "MRS_ECUDA", 4
 # Every symbol include/mrs_gb300.h declares (kept in sync by tests/test_abi.py).
 EXPORTS = [
     "mrs_last_error", "mrs_version", "mrs_ctx_create", "mrs_ctx_destroy", "mrs_ctx_num_sms",
+    "mrs_ctx_set_fused_steps",
     "mrs_velocity", "mrs_plan_create", "mrs_plan_execute", "mrs_plan_destroy",
     "mrs_plan_config_count", "mrs_plan_config_symmetric", "mrs_plan_config_info", "mrs_plan_info",
     "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run", "mrs_velocity_noalloc",
@@ -107,6 +108,7 @@ def lib():
         L.mrs_ctx_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
         L.mrs_ctx_destroy.argtypes = [_vp]
         L.mrs_ctx_num_sms.argtypes = [_vp]
+        L.mrs_ctx_set_fused_steps.argtypes = [_vp, ctypes.c_int]
         L.mrs_device_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint)]
         L.mrs_velocity.argtypes = [_vp, ctypes.c_int, _i64p, _vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _vp]
@@ -189,6 +191,11 @@ class Context:
     @property
     def num_sms(self) -> int:
         return int(lib().mrs_ctx_num_sms(self.handle))
+
+    def set_fused_steps(self, enable: bool) -> None:
+        """``mrs_ctx_set_fused_steps``: one fused launch per rod-stepping call for small
+        instances (default) or the per-step kernel graphs."""
+        _check(lib().mrs_ctx_set_fused_steps(self.handle, 1 if enable else 0))
 
     def device_status(self) -> int:
         """``mrs_device_status``: anomaly flags since the last call (synchronizes, clears)."""

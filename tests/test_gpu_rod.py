@@ -307,3 +307,54 @@ def test_parareal_reports_non_convergence(ctx):
     st = mrs.parareal_run(ctx, rs.rod_off, gs, Xd, Dd, 0.0, 4 * 64 * 1e-4, 4, 1e-4, 64, 4, 1e-10,
                           raise_on_noconv=False)
     assert not (st.final_incr < 1e-10)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_fused_and_graph_stepping_agree(ctx, orc, scheme):
+    """The fused path (one launch per call, state in shared memory; the default for small
+    instances) and the per-step kernel graphs compute the same steps: 200 steps of the
+    128-node rod and of four interacting 64-node rods agree to float32 rounding of the pair
+    sum, and both match the oracle."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    cases = [(W.rod_system(1, 1, 128), dict(W.ROD_PLAIN), 0.0, W.ROD_PLAIN["dt"]),
+             (W.rod_system(73, 4, 64, box=2.0), dict(W.ROD_PLAIN, a=(2e-3,) * 3, b=(20.0,) * 3),
+              0.1, 2e-6)]
+    for rs, cfg, t0, dt in cases:
+        gp, op = params(cfg, rs.eps)
+        out = []
+        try:
+            for fused in (True, False):
+                ctx.set_fused_steps(fused)
+                Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+                mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, t0, dt, 200, scheme)
+                torch.cuda.synchronize()
+                out.append((Xd.cpu().numpy(), Dd.cpu().numpy()))
+        finally:
+            ctx.set_fused_steps(True)
+        (Xf, Df), (Xg, Dg) = out
+        assert rel(Xf - rs.X, Xg - rs.X) < 1e-5
+        assert rel(Df - rs.D, Dg - rs.D) < 1e-4
+        Xo, _ = orc.rod_step(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, t0, dt, 200, scheme)
+        assert rel(Xf - rs.X, Xo - rs.X) < 1e-4
+
+
+def test_parareal_fused_and_graph_fine_solves_agree(ctx):
+    """Parareal whose fine and coarse solves run fused (one launch per solve, one CTA per
+    slice) reaches the same state as with the per-step kernel graphs."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(74, 2, 24, box=1.5)
+    cfg = dict(W.WAVE, a=(2e-3,) * 3, b=(0.3,) * 3)
+    gp, _ = params(cfg, rs.eps)
+    Ns, dt, r = 6, 5e-5, 4
+    T1 = Ns * 16 * dt
+    res = []
+    try:
+        for fused in (True, False):
+            ctx.set_fused_steps(fused)
+            Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+            st = mrs.parareal_run(ctx, rs.rod_off, gp, Xd, Dd, 0.0, T1, Ns, dt, r, Ns, 1e-10)
+            res.append((Xd.cpu().numpy(), st.iterations))
+    finally:
+        ctx.set_fused_steps(True)
+    assert rel(res[0][0] - rs.X, res[1][0] - rs.X) < 1e-5
+    assert abs(res[0][1] - res[1][1]) <= 1
