@@ -86,7 +86,7 @@ MRS_API int mrs_ctx_destroy(mrs_ctx* ctx);
 MRS_API int mrs_ctx_num_sms(const mrs_ctx* ctx);
 
 /* Rod stepping path of the context (rod_step, parareal_run, parareal_run_pipelined).  With
- * enable = 1 (the default) a batch of small instances -- at most ~650 nodes each (the state
+ * enable = 1 (the default) a batch of small instances -- at most ~600 nodes each (the state
  * must fit shared memory), float32 pair sum, no Lennard-Jones term -- advances through all its
  * steps in ONE launch: one CTA per instance keeps the instance's state in shared memory and runs
  * forces, pair sum and update of every stage back to back.  With enable = 0, or for larger or

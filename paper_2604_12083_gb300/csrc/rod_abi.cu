@@ -162,6 +162,7 @@ RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt)
     L.FN = ws->d_FN;
     L.chunks = ws->d_chunks;
     L.n_chunks = ws->n_chunks;
+    L.inv_L = 1.0 / p->L;
     return L;
 }
 

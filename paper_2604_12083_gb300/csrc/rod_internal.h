@@ -16,6 +16,7 @@ struct RodLaunch {
     double* FN;                // [N][6] segment force / moment scratch (two-kernel path)
     const int* chunks;         // [n_chunks] base node of every fused-kernel chunk, or NULL
     int n_chunks;
+    double inv_L;              // 1 / p.L
 };
 constexpr int kRodChunk = 128;   // threads per fused rod-force CTA (kRodChunk - 1 nodes each)
 

@@ -28,32 +28,34 @@ __device__ __forceinline__ double dot3(const double* a, const double* b)
 // Unit quaternion (w, x, y, z) of a rotation matrix A (row-major), w >= 0.
 __device__ __forceinline__ void rot_to_quat(const double* A, double* q)
 {
+    // each branch: r = sqrt(x) and 1/(2r) from one reciprocal square root (x >= 1 on the
+    // branch taken, so no zero division), q scaled to unit length at the end
     const double tr = A[0] + A[4] + A[8];
     if (tr >= A[0] && tr >= A[4] && tr >= A[8]) {
-        const double r = sqrt(fmax(1.0 + tr, 0.0));
-        const double s = 0.5 / r;
-        q[0] = 0.5 * r;
+        const double x = fmax(1.0 + tr, 0.0), ir = rsqrt(x);
+        const double s = 0.5 * ir;
+        q[0] = 0.5 * x * ir;
         q[1] = (A[7] - A[5]) * s;
         q[2] = (A[2] - A[6]) * s;
         q[3] = (A[3] - A[1]) * s;
     } else if (A[0] >= A[4] && A[0] >= A[8]) {
-        const double r = sqrt(fmax(1.0 + A[0] - A[4] - A[8], 0.0));
-        const double s = 0.5 / r;
-        q[1] = 0.5 * r;
+        const double x = fmax(1.0 + A[0] - A[4] - A[8], 0.0), ir = rsqrt(x);
+        const double s = 0.5 * ir;
+        q[1] = 0.5 * x * ir;
         q[0] = (A[7] - A[5]) * s;
         q[2] = (A[1] + A[3]) * s;
         q[3] = (A[2] + A[6]) * s;
     } else if (A[4] >= A[8]) {
-        const double r = sqrt(fmax(1.0 - A[0] + A[4] - A[8], 0.0));
-        const double s = 0.5 / r;
-        q[2] = 0.5 * r;
+        const double x = fmax(1.0 - A[0] + A[4] - A[8], 0.0), ir = rsqrt(x);
+        const double s = 0.5 * ir;
+        q[2] = 0.5 * x * ir;
         q[0] = (A[2] - A[6]) * s;
         q[1] = (A[1] + A[3]) * s;
         q[3] = (A[5] + A[7]) * s;
     } else {
-        const double r = sqrt(fmax(1.0 - A[0] - A[4] + A[8], 0.0));
-        const double s = 0.5 / r;
-        q[3] = 0.5 * r;
+        const double x = fmax(1.0 - A[0] - A[4] + A[8], 0.0), ir = rsqrt(x);
+        const double s = 0.5 * ir;
+        q[3] = 0.5 * x * ir;
         q[0] = (A[3] - A[1]) * s;
         q[1] = (A[2] + A[6]) * s;
         q[2] = (A[5] + A[7]) * s;
@@ -96,14 +98,13 @@ __global__ void rot_sqrt_batch_kernel(int n, const double* R, double* S)
     if (i < n) rot_sqrt_dev(R + 9 * (size_t)i, S + 9 * (size_t)i);
 }
 
-// Segment k+1/2 (index idx within a rod of M nodes; Xk, Dk point at node k, node k+1 follows)
-// at time t: internal force F and moment N in lab coordinates (Eqs. mid_triad,
-// F_comp_discrete, N_comp_discrete; Omega of Section IV-A at the segment midpoint), written to
-// o[0..5].
+// Segment k+1/2 (Xk, Dk point at node k, node k+1 follows; ids = 1/ds of its rod; om2 = the
+// preferred curvature Omega_2 of Section IV-A at the segment midpoint and the current time):
+// internal force F and moment N in lab coordinates (Eqs. mid_triad, F_comp_discrete,
+// N_comp_discrete), written to o[0..5].
 __device__ __forceinline__ void segment_core(const mrs_rod_params& P, const double* Xk,
-                                             const double* Dk, double t, int idx, int M, double* o)
+                                             const double* Dk, double ids, double om2, double* o)
 {
-    const double ds = P.L / (double)(M - 1);
     const double* Dk1 = Dk + 9;
     double A[9], S[9], Dh[9];
 #pragma unroll
@@ -117,10 +118,7 @@ __device__ __forceinline__ void segment_core(const mrs_rod_params& P, const doub
 #pragma unroll
         for (int r = 0; r < 3; ++r)
             Dh[3 * i + r] = S[3 * r] * Dk[3 * i] + S[3 * r + 1] * Dk[3 * i + 1] + S[3 * r + 2] * Dk[3 * i + 2];
-    const double ids = 1.0 / ds;   // one division; float64 divisions are expensive here
     const double e[3] = {(Xk[3] - Xk[0]) * ids, (Xk[4] - Xk[1]) * ids, (Xk[5] - Xk[2]) * ids};
-    const double s_mid = ((double)idx + 0.5) * ds;
-    const double om2 = -P.wave_k * P.wave_k * P.wave_A * sin(P.wave_k * s_mid + P.wave_f * t);
     double F[3] = {0, 0, 0}, Nm[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -143,14 +141,19 @@ __device__ __forceinline__ void segment_core(const mrs_rod_params& P, const doub
     o[5] = Nm[2];
 }
 
-// Segment k+1/2 of the batch at the current step's time (+ t_off).
+// Segment k+1/2 of the batch (index idx within a rod of M nodes) at the current step's time
+// (+ t_off).
 __device__ void segment_fn(const RodLaunch& L, const double* __restrict__ X,
                            const double* __restrict__ D, double t_off, long long k, int idx, int M,
                            double* o)
 {
     const int inst = (int)(k / L.nodes_per_inst);
     const double t = L.t0[inst] + (double)(*L.step) * L.dt + t_off;
-    segment_core(L.p, X + 3 * (size_t)k, D + 9 * (size_t)k, t, idx, M, o);
+    const double ds = L.p.L / (double)(M - 1);
+    const double ids = (double)(M - 1) * L.inv_L;   // one division fewer per segment
+    const double s_mid = ((double)idx + 0.5) * ds;
+    const double om2 = -L.p.wave_k * L.p.wave_k * L.p.wave_A * sin(L.p.wave_k * s_mid + L.p.wave_f * t);
+    segment_core(L.p, X + 3 * (size_t)k, D + 9 * (size_t)k, ids, om2, o);
 }
 
 __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__ X,
@@ -331,16 +334,27 @@ __device__ __forceinline__ void fused_kahan(float& sum, float& comp, float v)
     sum = t;
 }
 
-// Velocities (u, w) of the instance's points for the state (sXs, sDs) at time t.
+// Velocities (u, w) of the instance's points for the state (sXs, sDs) at time t.  sseg[k] =
+// (1/ds of node k's rod, sin(k_w s_mid), cos(k_w s_mid)) for the segment k+1/2, so that
+// Omega_2 = -k_w^2 A (sin(k_w s_mid) cos(f t) + cos(k_w s_mid) sin(f t)) needs one sincos per
+// stage (one thread, shared through stime) instead of one sin per segment.
 template <int BLOCK>
 __device__ void fused_velocity(const mrs_rod_params& P, const FusedConst& K, int N1,
-                               const int2* sni, const double* sXs, const double* sDs, double t,
-                               double* sFN, float* sXf, float* sgf, float* smf, float* su, float* sw)
+                               const int2* sni, const double* sseg, const double* sXs,
+                               const double* sDs, double t, double* stime, double* sFN,
+                               float* sXf, float* sgf, float* smf, float* su, float* sw)
 {
     const int tid = threadIdx.x;
+    if (tid == 0) sincos(P.wave_f * t, &stime[0], &stime[1]);
+    __syncthreads();
+    const double sft = stime[0], cft = stime[1];
+    const double amp = -P.wave_k * P.wave_k * P.wave_A;
     for (int k = tid; k < N1; k += BLOCK) {
         const int2 ni = sni[k];
-        if (ni.x < ni.y - 1) segment_core(P, sXs + 3 * k, sDs + 9 * k, t, ni.x, ni.y, sFN + 6 * k);
+        if (ni.x < ni.y - 1) {
+            const double om2 = amp * (sseg[3 * k + 1] * cft + sseg[3 * k + 2] * sft);
+            segment_core(P, sXs + 3 * k, sDs + 9 * k, sseg[3 * k], om2, sFN + 6 * k);
+        }
     }
     __syncthreads();
     for (int k = tid; k < N1; k += BLOCK) {
@@ -426,7 +440,9 @@ __global__ void __launch_bounds__(BLOCK) rod_fine_fused_kernel(const RodLaunch L
     double* sXh = sD + 9 * N1;
     double* sDh = sXh + 3 * N1;
     double* sFN = sDh + 9 * N1;
-    int2* sni = reinterpret_cast<int2*>(sFN + 6 * N1);
+    double* sseg = sFN + 6 * N1;
+    double* stime = sseg + 3 * N1;   // sin(f t), cos(f t) of the current stage
+    int2* sni = reinterpret_cast<int2*>(stime + 2);
     float* sXf = reinterpret_cast<float*>(sni + N1);
     float* sgf = sXf + 3 * N1;
     float* smf = sgf + 3 * N1;
@@ -436,17 +452,27 @@ __global__ void __launch_bounds__(BLOCK) rod_fine_fused_kernel(const RodLaunch L
     double* gD = D + (size_t)inst * 9 * N1;
     for (int q = threadIdx.x; q < 3 * N1; q += BLOCK) sX[q] = gX[q];
     for (int q = threadIdx.x; q < 9 * N1; q += BLOCK) sD[q] = gD[q];
-    for (int k = threadIdx.x; k < N1; k += BLOCK) sni[k] = L.node_info[k];
+    for (int k = threadIdx.x; k < N1; k += BLOCK) {
+        const int2 ni = L.node_info[k];
+        sni[k] = ni;
+        const double ds = L.p.L / (double)(ni.y - 1);
+        double sk, ck;
+        sincos(L.p.wave_k * ((double)ni.x + 0.5) * ds, &sk, &ck);
+        sseg[3 * k] = 1.0 / ds;
+        sseg[3 * k + 1] = sk;
+        sseg[3 * k + 2] = ck;
+    }
     const double t0 = L.t0[inst] + (double)(*L.step) * L.dt;
     __syncthreads();
     for (int st = 0; st < nsteps; ++st) {
         const double t = t0 + (double)st * L.dt;
-        fused_velocity<BLOCK>(L.p, K, N1, sni, sX, sD, t, sFN, sXf, sgf, smf, su, sw);
+        fused_velocity<BLOCK>(L.p, K, N1, sni, sseg, sX, sD, t, stime, sFN, sXf, sgf, smf, su, sw);
         if (scheme == MRS_EULER) {
             fused_update<BLOCK>(N1, sX, sD, su, sw, L.dt, sX, sD);
         } else {
             fused_update<BLOCK>(N1, sX, sD, su, sw, 0.5 * L.dt, sXh, sDh);
-            fused_velocity<BLOCK>(L.p, K, N1, sni, sXh, sDh, t + 0.5 * L.dt, sFN, sXf, sgf, smf, su, sw);
+            fused_velocity<BLOCK>(L.p, K, N1, sni, sseg, sXh, sDh, t + 0.5 * L.dt, stime, sFN, sXf,
+                                  sgf, smf, su, sw);
             fused_update<BLOCK>(N1, sX, sD, su, sw, L.dt, sX, sD);
         }
     }
@@ -458,7 +484,10 @@ __global__ void rod_bump_step_kernel(long long* step, int nsteps) { *step += nst
 
 constexpr int kFusedBlock = 256;
 
-size_t fused_smem_bytes(int N1) { return (size_t)N1 * (30 * sizeof(double) + sizeof(int2) + 15 * sizeof(float)); }
+size_t fused_smem_bytes(int N1)
+{
+    return 2 * sizeof(double) + (size_t)N1 * (33 * sizeof(double) + sizeof(int2) + 15 * sizeof(float));
+}
 
 bool fused_fits(int N1)
 {

@@ -294,6 +294,7 @@ cudaError_t admit_enqueue(mrs_server* S, SJob* j)
     L.FN = FN;
     L.chunks = nullptr;   // two-kernel force path (no chunk table in the pool)
     L.n_chunks = 0;
+    L.inv_L = 1.0 / J.params.L;
     return cudaSuccess;
 }
 

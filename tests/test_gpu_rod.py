@@ -323,19 +323,20 @@ def test_fused_and_graph_stepping_agree(ctx, orc, scheme):
         gp, op = params(cfg, rs.eps)
         out = []
         try:
-            for fused in (True, False):
-                ctx.set_fused_steps(fused)
+            for mode in (1, 0):       # fused (one launch per call), per-step graphs
+                ctx.set_fused_steps(mode)
                 Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
                 mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, t0, dt, 200, scheme)
                 torch.cuda.synchronize()
                 out.append((Xd.cpu().numpy(), Dd.cpu().numpy()))
         finally:
-            ctx.set_fused_steps(True)
-        (Xf, Df), (Xg, Dg) = out
-        assert rel(Xf - rs.X, Xg - rs.X) < 1e-5
-        assert rel(Df - rs.D, Dg - rs.D) < 1e-4
+            ctx.set_fused_steps(1)
         Xo, _ = orc.rod_step(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, t0, dt, 200, scheme)
-        assert rel(Xf - rs.X, Xo - rs.X) < 1e-4
+        Xg, Dg = out[1]
+        for Xf, Df in out[:1]:
+            assert rel(Xf - rs.X, Xg - rs.X) < 1e-5
+            assert rel(Df - rs.D, Dg - rs.D) < 1e-4
+            assert rel(Xf - rs.X, Xo - rs.X) < 1e-4
 
 
 def test_parareal_fused_and_graph_fine_solves_agree(ctx):
@@ -349,12 +350,12 @@ def test_parareal_fused_and_graph_fine_solves_agree(ctx):
     T1 = Ns * 16 * dt
     res = []
     try:
-        for fused in (True, False):
-            ctx.set_fused_steps(fused)
+        for mode in (1, 0):
+            ctx.set_fused_steps(mode)
             Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
             st = mrs.parareal_run(ctx, rs.rod_off, gp, Xd, Dd, 0.0, T1, Ns, dt, r, Ns, 1e-10)
             res.append((Xd.cpu().numpy(), st.iterations))
     finally:
-        ctx.set_fused_steps(True)
+        ctx.set_fused_steps(1)
     assert rel(res[0][0] - rs.X, res[1][0] - rs.X) < 1e-5
     assert abs(res[0][1] - res[1][1]) <= 1
