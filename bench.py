@@ -238,9 +238,8 @@ def _time_events(fn, reps, stream):
 
 def extra_batch(ctx, dev):
     """512 systems (256..16384 points): one persistent launch (CUDA graph) vs one launch per
-    system, float32 accumulation; rel L2 of 4 sampled targets per system."""
+    system, float32 accumulation (accuracy against the oracle: the GPU tests)."""
     import torch
-    import oracle
     from paper_2604_12083_gb300 import mrs, workloads as W
     p = W.batch_systems()
     X, f, n = (torch.from_numpy(a).to(dev) for a in (p.X, p.f, p.n))
@@ -262,16 +261,6 @@ def extra_batch(ctx, dev):
     g.replay()
     torch.cuda.synchronize()
     ms_graph = _time_events(g.replay, 5, stream)
-    rng = np.random.default_rng(12)
-    en = ed = wn = wd = 0.0
-    ug, wg = u.cpu().numpy().astype(np.float64), w.cpu().numpy().astype(np.float64)
-    for s in range(0, len(p.offsets) - 1):
-        a, b = int(p.offsets[s]), int(p.offsets[s + 1])
-        idx = rng.choice(b - a, 4, replace=False)
-        ur, wr = oracle.mrs_velocity(p.X[a:b], p.f[a:b], p.n[a:b], p.eps[s], p.mu, xt=p.X[a:b][idx])
-        en += np.sum((ug[a:b][idx] - ur) ** 2); ed += np.sum(ur ** 2)
-        wn += np.sum((wg[a:b][idx] - wr) ** 2); wd += np.sum(wr ** 2)
-    rel_batch = {"u": float(np.sqrt(en / ed)), "w": float(np.sqrt(wn / wd))}
     plans = []
     for s in range(len(p.offsets) - 1):
         a, b = int(p.offsets[s]), int(p.offsets[s + 1])
@@ -294,7 +283,7 @@ def extra_batch(ctx, dev):
             "persistent_pairs_per_s": p.pairs / (ms_graph * 1e-3),
             "one_launch_per_system_ms": ms_loop,
             "one_launch_per_system_pairs_per_s": p.pairs / (ms_loop * 1e-3),
-            "speedup": ms_loop / ms_graph, "rel_err_sampled": rel_batch, "plan": info,
+            "speedup": ms_loop / ms_graph, "plan": info,
             "autotuned_config": tuned_cfg, "autotune_best_ms": tuned_ms}
 
 
@@ -619,18 +608,10 @@ def run_ours(args, world, rank, local, pg):
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     value, ms_per_step = aggregate(pg, dev, launch_ms, p.pairs, args.steps)
 
-    # ---- parity on sampled targets (oracle, rank 0 only; outside the timed region) ----
+    # the last timed step's result, for the accuracy figure of the CPU-baseline leg
+    u_last = u.cpu().numpy().astype(np.float64)
+    w_last = w.cpu().numpy().astype(np.float64)
     rel = None
-    if rank == 0:
-        import oracle
-        oracle.build()
-        idx = np.random.default_rng(9).choice(p.n_points, 256, replace=False)
-        ur, wr = oracle.mrs_velocity(p.X, p.f, p.n, eps, p.mu, xt=p.X[idx])
-        ug = u.cpu().numpy().astype(np.float64)[idx]
-        wg = w.cpu().numpy().astype(np.float64)[idx]
-        rel = {"u": float(np.linalg.norm(ug - ur) / np.linalg.norm(ur)),
-               "w": float(np.linalg.norm(wg - wr) / np.linalg.norm(wr)),
-               "targets_sampled": 256}
 
     # ---- end to end through the public API with host buffers ----
     # Every step copies its inputs from pinned host memory and its result back.  The copies run
@@ -722,15 +703,21 @@ def run_ours(args, world, rank, local, pg):
         args.cpu_baseline = False
         args.extras = False
     if rank == 0 and args.cpu_baseline:
+        # the FP64 oracle on a sample of targets (about 10 s of host work), timed; its values on
+        # those targets also give the accuracy of the GPU result (relative L2 per field)
         import oracle
         nt, _ = oracle_rate(p, 10.0)
         idx = np.random.default_rng(11).choice(p.n_points, nt, replace=False)
         t0 = time.perf_counter()
-        oracle.mrs_velocity(p.X, p.f, p.n, eps, p.mu, xt=p.X[idx])
+        ur, wr = oracle.mrs_velocity(p.X, p.f, p.n, eps, p.mu, xt=p.X[idx])
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": nt * p.n_points / dt, "unit": UNIT,
                                 "cores": oracle.num_threads(), "kind": "oracle",
                                 "sample": "%d sampled targets x %d sources (FP64)" % (nt, p.n_points)}
+        line["rel_err"] = {
+            "u": float(np.linalg.norm(u_last[idx] - ur) / np.linalg.norm(ur)),
+            "w": float(np.linalg.norm(w_last[idx] - wr) / np.linalg.norm(wr)),
+            "targets_sampled": int(nt), "against": "the FP64 oracle of the cpu_baseline sample"}
     line["frac_of_fp32_peak"] = line["roofline"]["frac"]
     if rank == 0 and args.extras:
         line["extras"] = run_extras(ctx, dev)
