@@ -744,8 +744,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--config", type=int, default=-1,
                     help="force this pair-sum plan configuration (default: the library's choice)")
-    ap.add_argument("--case", choices=["main", "rod_kernels"], default="main",
-                    help="rod_kernels: time the rod force and update kernels on 1M nodes")
+    ap.add_argument("--case", choices=["main", "rod_kernels", "parareal"], default="main",
+                    help="rod_kernels: time the rod force and update kernels on 1M nodes; "
+                         "parareal: the Parareal measurements alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -757,6 +758,14 @@ def main():
         return
     if args.case == "rod_kernels":
         run_rod_kernels(args)
+        return
+    if args.case == "parareal":
+        import torch
+        from paper_2604_12083_gb300 import build as B, mrs
+        B.build()
+        ctx = mrs.Context(0)
+        print(json.dumps({"case": "parareal", **extra_parareal(ctx, torch.device("cuda", 0))}), flush=True)
+        ctx.close()
         return
     world, rank, local, pg = dist_setup()
     run_ours(args, world, rank, local, pg)

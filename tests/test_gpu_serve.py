@@ -80,7 +80,8 @@ def test_results_same_alone_and_in_mix(ctx):
         others = []
         for i in range(12):
             others.append(run_velocity(srv, vjobs[i])[1])
-            others.append(run_rod(srv, rjobs[i], nsteps=3 + i % 5)[1])
+            # long enough (40+ steps) to be still running when the measured jobs join
+            others.append(run_rod(srv, rjobs[i], nsteps=40 + i % 5)[1])
         tv2, bv2 = run_velocity(srv, pv)
         tr2, br2 = run_rod(srv, pr)
         srv.drain()
