@@ -87,11 +87,11 @@ MRS_API int mrs_ctx_num_sms(const mrs_ctx* ctx);
 
 /* Rod stepping path of the context (rod_step, parareal_run, parareal_run_pipelined).  With
  * enable = 1 (the default) a batch of small instances -- at most ~600 nodes each (the state
- * must fit shared memory), float32 pair sum, no Lennard-Jones term -- advances through all its
- * steps in ONE launch: one CTA per instance keeps the instance's state in shared memory and runs
- * forces, pair sum and update of every stage back to back.  With enable = 0, or for larger or
- * Lennard-Jones instances, every step is forces -> pair-sum plan -> update kernels replayed from
- * captured CUDA graphs.  Both compute the same steps; results agree to float32 rounding of the
+ * must fit shared memory), float32 pair sum -- advances through all its steps in ONE launch:
+ * one CTA per instance keeps the instance's state in shared memory and runs forces (with the
+ * Lennard-Jones repulsion when enabled), pair sum and update of every stage back to back.  With
+ * enable = 0, or for larger instances or MRS_F64, every step is forces -> pair-sum plan ->
+ * update kernels replayed from captured CUDA graphs.  Both compute the same steps; results agree to float32 rounding of the
  * pair sum.  Host only.  Errors: MRS_EINVAL. */
 MRS_API int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable);
 

@@ -280,9 +280,9 @@ int rod_ws_steps(RodWorkspace* ws, const mrs_rod_params* p, double* X, double* D
                  int nsteps, int scheme, cudaStream_t s)
 {
     if (nsteps <= 0 || ws->N == 0) return MRS_OK;
-    // small instances without Lennard-Jones: every step of every instance in one launch, the
-    // state in shared memory (one CTA per instance)
-    if (ws->ctx->fused_steps && ws->precision != MRS_F64 && p->lj_eps == 0.0 && fused_fits(ws->N1)) {
+    // small instances: every step of every instance in one launch, the state in shared memory
+    // (one CTA per instance)
+    if (ws->ctx->fused_steps && ws->precision != MRS_F64 && fused_fits(ws->N1)) {
         const RodLaunch L = rod_launch(ws, p, dt);
         cudaError_t e = launch_rod_fine_fused(L, X, D, nsteps, scheme, p->mu, p->eps, s);
         if (e != cudaSuccess) {

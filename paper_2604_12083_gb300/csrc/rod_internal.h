@@ -32,8 +32,7 @@ cudaError_t launch_rod_update64(const RodLaunch& L, const double* X0, const doub
 cudaError_t launch_rot_sqrt_batch(int n, const double* R, double* S, cudaStream_t s);
 // Fused fine propagator (one CTA per instance, state in shared memory): nsteps steps of size
 // L.dt of every instance of the batch in one launch, then the step counter advances by nsteps.
-// Usable when the instance fits shared memory (fused_fits) -- float32 pair sum, no
-// Lennard-Jones term.
+// Usable when the instance fits shared memory (fused_fits) -- float32 pair sum.
 constexpr size_t kFusedMaxSmem = 200 * 1024;
 size_t fused_smem_bytes(int N1);
 bool fused_fits(int N1);

@@ -312,8 +312,8 @@ __global__ void rod_update_kernel(const RodLaunch L, const double* X0, const dou
 // stage runs the same arithmetic as the batched kernels: segment_core (rotation square root,
 // internal force and moment), node_fn (node force and torque, float32 packs), the regularized
 // Stokeslet pair sum over the instance's points (float32, per-target accumulation in 32-source
-// chunks folded into Kahan pairs; the kernels written with d s^2 = 1 as in mrs_kernels.cu) and
-// rodrigues (Eqs. newx, newD).  Only __syncthreads separates the phases: no launches per step.
+// chunks folded into Kahan pairs; the kernels written with d s^2 = 1 as in mrs_kernels.cu), the
+// Lennard-Jones repulsion between its rods when enabled, and rodrigues (Eqs. newx, newD).  Only __syncthreads separates the phases: no launches per step.
 // ---------------------------------------------------------------------------------------------
 struct FusedConst {   // pair-sum constants of the instance's system (see SysConst)
     float e2, c1, c2, c3, c5, scale;
@@ -363,6 +363,38 @@ __device__ void fused_velocity(const mrs_rod_params& P, const FusedConst& K, int
                 nullptr, nullptr, sXf, sgf, smf);
     }
     __syncthreads();
+    if (P.lj_eps > 0.0) {
+        // Section IV-A repulsion between nodes of different rods of the instance, as in
+        // rod_lj_kernel: float32 screen against r_c^2 with a 1 % margin, float64 force for the
+        // close pairs, added to the force the node applies to the fluid
+        const double s2 = P.lj_sigma * P.lj_sigma;
+        const double rc2 = 1.2599210498948732 * s2;            // (2^{1/6} sigma)^2
+        const float rc2f = (float)(1.01 * rc2);
+        for (int k = tid; k < N1; k += BLOCK) {
+            const int key = k - sni[k].x;
+            const float xf = sXf[3 * k], yf = sXf[3 * k + 1], zf = sXf[3 * k + 2];
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            for (int j = 0; j < N1; ++j) {
+                const float dx = xf - sXf[3 * j], dy = yf - sXf[3 * j + 1], dz = zf - sXf[3 * j + 2];
+                if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rc2f && j - sni[j].x != key) {
+                    const double rx = sXs[3 * k] - sXs[3 * j], ry = sXs[3 * k + 1] - sXs[3 * j + 1],
+                                 rz = sXs[3 * k + 2] - sXs[3 * j + 2];
+                    const double r2 = rx * rx + ry * ry + rz * rz;
+                    if (r2 < rc2 && r2 > 0.0) {
+                        const double sr2 = s2 / r2, sr6 = sr2 * sr2 * sr2;
+                        const double c = 24.0 * P.lj_eps * (2.0 * sr6 * sr6 - sr6) / r2;
+                        a0 += c * rx;
+                        a1 += c * ry;
+                        a2 += c * rz;
+                    }
+                }
+            }
+            sgf[3 * k] = (float)((double)sgf[3 * k] + a0);
+            sgf[3 * k + 1] = (float)((double)sgf[3 * k + 1] + a1);
+            sgf[3 * k + 2] = (float)((double)sgf[3 * k + 2] + a2);
+        }
+        __syncthreads();
+    }
     for (int i = tid; i < N1; i += BLOCK) {
         const float xi = sXf[3 * i], yi = sXf[3 * i + 1], zi = sXf[3 * i + 2];
         float sum[6], cmp[6];

@@ -359,3 +359,35 @@ def test_parareal_fused_and_graph_fine_solves_agree(ctx):
         ctx.set_fused_steps(1)
     assert rel(res[0][0] - rs.X, res[1][0] - rs.X) < 1e-5
     assert abs(res[0][1] - res[1][1]) <= 1
+
+
+def test_fused_and_graph_stepping_agree_with_lj(ctx):
+    """Two parallel rods 0.12 apart, inside the Lennard-Jones cut-off 2^(1/6) sigma = 0.129,
+    60 RK2 steps: the fused path (the repulsion evaluated inside the one-launch solve) and the
+    kernel graphs (rod_lj_kernel, pinned to the oracle by test_rod_forces_with_lj_match_oracle)
+    reach the same state, and the repulsion changes the motion."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    M = 40
+    X1, D1 = W.sinusoid_filament(M)
+    X = np.concatenate([X1, X1 + np.array([0.0, 0.0, 0.12])])
+    D = np.concatenate([D1, D1])
+    off = np.array([0, M, 2 * M], np.int64)
+    eps = 1.5 / (M - 1)                                     # sigma = 3 eps = 0.115
+    cfg = dict(W.ROD_PLAIN, a=(2e-3,) * 3, b=(20.0,) * 3)
+    out = {}
+    try:
+        for lj in (0.0, 0.05):
+            gp = mrs.RodParams.make(cfg["L"], cfg["a"], cfg["b"], cfg["wave_A"], cfg["wave_k"],
+                                    cfg["wave_f"], 1.0, eps, lj_eps=lj)
+            for fused in (1, 0):
+                ctx.set_fused_steps(fused)
+                Xd, Dd = torch.from_numpy(X.copy()).cuda(), torch.from_numpy(D.copy()).cuda()
+                mrs.rod_step(ctx, off, gp, Xd, Dd, 0.0, 2e-6, 60, mrs.MRS_RK2)
+                torch.cuda.synchronize()
+                out[(lj, fused)] = Xd.cpu().numpy()
+    finally:
+        ctx.set_fused_steps(1)
+    assert np.isfinite(out[(0.05, 1)]).all()
+    assert rel(out[(0.05, 1)] - X, out[(0.05, 0)] - X) < 1e-5
+    assert rel(out[(0.0, 1)] - X, out[(0.0, 0)] - X) < 1e-5
+    assert rel(out[(0.05, 0)] - X, out[(0.0, 0)] - X) > 1e-3      # the repulsion acts
