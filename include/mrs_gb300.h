@@ -146,7 +146,7 @@ MRS_API int mrs_velocity(mrs_ctx* ctx, int n_sys, const int64_t* offsets,
  *   X, f, n      device float32 [n_points][3] positions, forces, torques (caller-owned)
  *   u, w         device float32 [n_points][3] outputs (caller-owned, overwritten)
  *   mu, eps      viscosity (> 0) and regularisation (> 0)
- * Scratch (work table, partial results, tile counters) lives in a fixed ~18.3 MiB __device__
+ * Scratch (work table, partial results, tile counters) lives in a fixed ~9.1 MiB __device__
  * array that every GPU loading the library holds until the process exits.  The FIRST call on a
  * device looks up that array's device address (cudaGetSymbolAddress) and the device's SM count;
  * make that first call before any stream capture.  No call allocates or frees memory.  Every

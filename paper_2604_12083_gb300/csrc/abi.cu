@@ -50,16 +50,18 @@ int default_ordered_config(int n_sys, const int64_t* offsets)
 {
     // Measured on GB300: the packed f32x2 variants are fastest.  256 threads x 2 targets
     // (512-target tiles) for systems of tens of thousands of points; when most points sit in
-    // systems of at most 8192 points, 256 threads x 1 target with the source loop unrolled twice
-    // for a few systems (a single 4096-point system: 45 us against 59 us), and 64 threads x 4
-    // targets (256-target tiles, 8 CTAs per SM) for many (64 systems of 4096 points: 1.69 ms
-    // against 1.77 ms).  mrs_autotune overrides all three.
-    int64_t small = 0, total = offsets[n_sys];
+    // systems of at most 8192 points, for a few systems 256 threads x 1 target with the source
+    // loop unrolled twice (a single 4096-point system: 41 us against 50 us with 512-target
+    // tiles), or 128 threads x 1 target when no system exceeds 1536 points (1024 points: 10.3
+    // against 12.4 us), and 64 threads x 4 targets (256-target tiles, 8 CTAs per SM) for many
+    // (64 systems of 4096 points: 1.69 ms against 1.77 ms).  mrs_autotune overrides all of them.
+    int64_t small = 0, total = offsets[n_sys], largest = 0;
     for (int s = 0; s < n_sys; ++s) {
         const int64_t ns = offsets[s + 1] - offsets[s];
         if (ns <= 8192) small += ns;
+        largest = std::max(largest, ns);
     }
-    if (total > 0 && small * 2 > total) return n_sys >= 16 ? 8 : 14;
+    if (total > 0 && small * 2 > total) return n_sys >= 16 ? 8 : largest <= 1536 ? 13 : 14;
     return 9;
 }
 
@@ -280,10 +282,11 @@ int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, doubl
         set_error("occupancy query failed for config %d", p->ocfg);
         return MRS_ECUDA;
     }
-    long long P = (long long)ctx->num_sms * occ * std::max(1, kc.over);
-    if (P > W) P = W;
+    long long max_nu = 0;
+    for (const TileDesc& T : tiles) max_nu = std::max<long long>(max_nu, T.nu);
+    const long long P = ordered_ctas((long long)ctx->num_sms * occ * std::max(1, kc.over), W, max_nu);
     p->P = (int)P;
-    const size_t part_floats = (size_t)2 * P * 12 * p->TM;
+    const size_t part_floats = (size_t)2 * P * 6 * p->TM;
     if ((st = dev_alloc(&p->d_tiles, tiles.size())) || (st = dev_alloc(&p->d_sc, sc.size())) ||
         (st = dev_alloc(&p->d_partial, part_floats)) || (st = dev_alloc(&p->d_counters, tiles.size()))) {
         plan_free(p);

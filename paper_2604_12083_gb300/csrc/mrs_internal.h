@@ -52,6 +52,27 @@ void clear_error();
 constexpr int kUnitSources = 32;   // sources per work unit (granularity of the CTA ranges)
 constexpr int kChunk = 256;        // sources staged in shared memory at a time
 
+// Persistent CTAs of an ordered launch over W units whose largest tile has max_nu units.  The
+// CTA that completes a tile reads the partial slot of every CTA that worked on it, one L2 round
+// trip per eight slots, while the other SMs idle at the end of the launch; for small systems
+// (few tiles, each cut over tens of CTAs with a unit or two each) that read dominated the call.
+// When the full grid would give a CTA fewer than kFewUnits units, the cut is capped at
+// kMaxSlotsPerTile CTAs per tile (measured on GB300: a single 2048-point system 26 -> 16.5 us,
+// 4096 points with 512-target tiles 50 -> 41 us).  With more work per CTA the full grid is
+// kept: a cap there leaves SMs with unequal numbers of resident CTAs (16384 points with
+// 512-target tiles: 486 -> 562 us when capped).
+constexpr int kMaxSlotsPerTile = 16;
+constexpr int kFewUnits = 4;
+inline long long ordered_ctas(long long P, long long W, long long max_nu)
+{
+    if (P > W) P = W;
+    if (max_nu > 0 && W < (long long)kFewUnits * P) {
+        const long long cap = (long long)kMaxSlotsPerTile * W / max_nu;
+        if (P > cap) P = cap;
+    }
+    return P < 1 ? 1 : P;
+}
+
 struct TileDesc {
     int sys;     // system index
     int t0;      // first target (global point index)
@@ -93,7 +114,7 @@ struct MrsLaunch {
     const float* Xt;      // targets (== X when none given)
     float* u;
     float* w;
-    float* partial;       // [2P][12][TM] floats
+    float* partial;       // [2P][6][TM] floats
     int* counters;        // [n_tiles], zero between launches
     unsigned int* err;    // device error word: bit 0 = a non-finite output was written
 };

@@ -345,7 +345,7 @@ mrs_f32_persistent(const MrsLaunch L)
             }
         } else {
             const int slot = 2 * p + (first_seg ? 0 : 1);
-            float* part = L.partial + (size_t)slot * 12 * TM;
+            float* part = L.partial + (size_t)slot * 6 * TM;
 #pragma unroll
             for (int k = 0; k < TPT; ++k) {
                 const int li = k * BLOCK + tid;
@@ -353,8 +353,7 @@ mrs_f32_persistent(const MrsLaunch L)
                 for (int q = 0; q < 6; ++q) {
                     if (COMP) {
                         const float2 sc2 = kah[(q * TPT + k) * BLOCK + tid];
-                        part[q * TM + li] = sc2.x;
-                        part[(6 + q) * TM + li] = sc2.y;
+                        part[q * TM + li] = __fsub_rn(sc2.x, sc2.y);
                     } else {
                         part[q * TM + li] = acc[k][q];
                     }
@@ -374,12 +373,14 @@ mrs_f32_persistent(const MrsLaunch L)
                 // Contributors are the consecutive CTAs q_lo..q_hi (every CTA range is non-empty
                 // because P <= W).  Only q_lo can have started before this tile, in which case
                 // the tile is its second segment (slot 2 q_lo + 1); for every later CTA it is the
-                // first segment (slot 2 qc).  Slots are read four at a time to keep loads in
-                // flight; the sum order stays the CTA order.
+                // first segment (slot 2 qc).  A slot holds one float per target and component
+                // (in MRS_F32_COMP the segment's Kahan pair folded to sum - compensation); they
+                // are read eight at a time to keep loads in flight, and the sum order stays the
+                // CTA order.
                 const int q_lo = cta_of_unit(L.W, L.P, T.u0);
                 const int q_hi = cta_of_unit(L.W, L.P, T.u0 + T.nu - 1);
                 const int sl_lo = 2 * q_lo + (unit_start(L.W, L.P, q_lo) < T.u0 ? 1 : 0);
-                constexpr int NV = COMP ? 12 : 6;
+                constexpr int NB = 8;
 #pragma unroll 1
                 for (int k = 0; k < TPT; ++k) {
                     const int li = k * BLOCK + tid;
@@ -389,23 +390,20 @@ mrs_f32_persistent(const MrsLaunch L)
                         tot[q] = 0.f;
                         cmp[q] = 0.f;
                     }
-                    for (int qb = q_lo; qb <= q_hi; qb += 4) {
-                        float v[4][NV];
+                    for (int qb = q_lo; qb <= q_hi; qb += NB) {
+                        float v[NB][6];
 #pragma unroll
-                        for (int bq = 0; bq < 4; ++bq) {
+                        for (int bq = 0; bq < NB; ++bq) {
                             const int qc = qb + bq;
                             const int sl = qc == q_lo ? sl_lo : 2 * qc;
-                            const float* pp = L.partial + (size_t)sl * 12 * TM + li;
+                            const float* pp = L.partial + (size_t)sl * 6 * TM + li;
 #pragma unroll
-                            for (int q = 0; q < NV; ++q) v[bq][q] = qc <= q_hi ? __ldcg(pp + q * TM) : 0.f;
+                            for (int q = 0; q < 6; ++q) v[bq][q] = qc <= q_hi ? __ldcg(pp + q * TM) : 0.f;
                         }
 #pragma unroll
-                        for (int bq = 0; bq < 4; ++bq)
+                        for (int bq = 0; bq < NB; ++bq)
 #pragma unroll
-                            for (int q = 0; q < 6; ++q) {
-                                kahan_add(tot[q], cmp[q], v[bq][q]);
-                                if (COMP) kahan_add(tot[q], cmp[q], -v[bq][(6 + q) % NV]);
-                            }
+                            for (int q = 0; q < 6; ++q) kahan_add(tot[q], cmp[q], v[bq][q]);
                     }
                     if (li < T.tn) {
                         const long long gi = (long long)T.t0 + li;

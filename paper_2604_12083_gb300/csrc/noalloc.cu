@@ -28,7 +28,7 @@ constexpr int kNaTM = 256;                           // targets per tile for tha
 constexpr long long kNaMaxPoints = 1LL << 20;        // largest accepted system
 constexpr int kNaMaxTiles = (int)(kNaMaxPoints / kNaTM);
 constexpr int kNaMaxCTAs = 768;                      // persistent CTAs (>= 5 per SM x 152 SMs)
-constexpr size_t kNaPartialBytes = (size_t)2 * kNaMaxCTAs * 12 * kNaTM * sizeof(float);
+constexpr size_t kNaPartialBytes = (size_t)2 * kNaMaxCTAs * 6 * kNaTM * sizeof(float);
 constexpr size_t kNaTilesBytes = (size_t)kNaMaxTiles * sizeof(TileDesc);
 constexpr size_t kNaCountersBytes = (size_t)kNaMaxTiles * sizeof(int);
 constexpr size_t kNaOffTiles = 0;
@@ -36,7 +36,7 @@ constexpr size_t kNaOffCounters = kNaOffTiles + kNaTilesBytes;
 constexpr size_t kNaOffConst = kNaOffCounters + kNaCountersBytes;
 constexpr size_t kNaOffErr = kNaOffConst + sizeof(SysConst);
 constexpr size_t kNaOffPartial = (kNaOffErr + sizeof(unsigned int) + 255) / 256 * 256;
-constexpr size_t kNaScratchBytes = kNaOffPartial + kNaPartialBytes;   // ~18.3 MiB
+constexpr size_t kNaScratchBytes = kNaOffPartial + kNaPartialBytes;   // ~9.1 MiB
 
 }  // namespace
 
@@ -129,7 +129,7 @@ extern "C" int mrs_velocity_noalloc(int64_t n_points, const float* X, const floa
     const int n_tiles = (N + kNaTM - 1) / kNaTM;
     const int nu = (N + kUnitSources - 1) / kUnitSources;
     const long long W = (long long)n_tiles * nu;
-    if (P > W) P = (int)W;
+    P = (int)ordered_ctas(P, W, nu);
     const double e2 = eps * eps;
     SysConst c;
     c.e2 = (float)e2;

@@ -365,7 +365,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
     const bool sym = (size_t)sW * kUnitSources * 6 <= S->colpart_cap &&
                      (size_t)nseg * S->sTM * 6 <= S->rowpart_cap;
     int nt = 0;
-    long long W = 0;
+    long long W = 0, max_nu = 0;
     if (!sym) {
         for (int q = 0; q < n_sys; ++q) {
             SJob* j = S->active[q];
@@ -381,6 +381,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
                 T.nu = nu;
                 T.u0 = W;
                 W += nu;
+                max_nu = std::max<long long>(max_nu, nu);
             }
         }
         if ((e = cudaMemcpyAsync(S->d_tiles, st.tiles, nt * sizeof(TileDesc), cudaMemcpyHostToDevice, s))) return e;
@@ -411,7 +412,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
         L.tiles = S->d_tiles;
         L.n_tiles = nt;
         L.W = W;
-        L.P = (int)std::min<long long>(S->P, W);
+        L.P = (int)ordered_ctas(S->P, W, max_nu);
         L.sc = S->d_sc;
         L.X = S->pX;
         L.f = S->pf;
@@ -617,7 +618,7 @@ int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int ma
         (st = dalloc(&S->pn, 3 * pt_cap)) || (st = dalloc(&S->pu, 3 * pt_cap)) ||
         (st = dalloc(&S->pw, 3 * pt_cap)) || (st = dalloc(&S->d_bytes, by_cap * kByteAlign)) ||
         (st = dalloc(&S->d_tiles, (size_t)S->tile_cap)) || (st = dalloc(&S->d_sc, (size_t)S->sys_cap)) ||
-        (st = dalloc(&S->d_partial, (size_t)2 * S->P * 12 * S->TM)) ||
+        (st = dalloc(&S->d_partial, (size_t)2 * S->P * 6 * S->TM)) ||
         (st = dalloc(&S->d_counters, (size_t)S->tile_cap)) ||
         (st = dalloc(&S->d_stiles, (size_t)S->tile_cap)) ||
         (st = dalloc(&S->d_rowpart, S->rowpart_cap)) || (st = dalloc(&S->d_colpart, S->colpart_cap))) {

@@ -149,6 +149,31 @@ def test_multi_tile_single_system(ctx, orc, config):
         assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
 
 
+@pytest.mark.parametrize("config", [None, 8, 9, 13, 14])
+def test_small_system_split_cap(ctx, orc, config):
+    """Single systems of 1024, 2048 and 4113 points (few tiles): where the full grid would give
+    each CTA fewer than 4 work units, an ordered plan cuts each tile over at most 16 CTAs (the
+    CTA that completes a tile reads at most 16 partial slots); otherwise it keeps the full grid.
+    The result matches the oracle either way."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    for M in (1024, 2048, 4113):
+        p = W.single_system(seed=M, n_fil=1, M=M)
+        pl = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32_COMP,
+                      config=-1 if config is None else config)
+        info = pl.info()
+        pl.close()
+        if not mrs.plan_config_symmetric(info["config"]):
+            ci = mrs.plan_config_info(ctx, info["config"])
+            tiles = -(-M // (ci["threads"] * ci["targets_per_thread"]))
+            assert info["grid"] >= 1
+            assert info["grid"] <= 16 * tiles or info["work_units"] >= 4 * info["grid"], (M, info)
+            if M <= 2048:                       # a few units per CTA at most: the cap binds
+                assert info["grid"] <= 16 * tiles, (M, info)
+        ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+        u, w = run(ctx, p, mrs.MRS_F32_COMP, config=config)
+        assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32, M
+
+
 @pytest.mark.parametrize("config", SYM_CONFIGS)
 def test_symmetric_plan_with_targets(ctx, orc, config):
     """A symmetric plan given targets equal to the sources (the same buffer) takes the
