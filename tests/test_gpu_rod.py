@@ -391,3 +391,52 @@ def test_fused_and_graph_stepping_agree_with_lj(ctx):
     assert rel(out[(0.05, 1)] - X, out[(0.05, 0)] - X) < 1e-5
     assert rel(out[(0.0, 1)] - X, out[(0.0, 0)] - X) < 1e-5
     assert rel(out[(0.05, 0)] - X, out[(0.0, 0)] - X) > 1e-3      # the repulsion acts
+
+
+@pytest.mark.parametrize("group_size", [0, 8])
+def test_parareal_full_size_workload(ctx, orc, group_size):
+    """The Parareal workload at full size and in the launch configuration the benchmark times:
+    8 filaments x 512 nodes, 64 slices x 16 fine RK2 steps (dt = 1e-6), coarse Euler 4 dt,
+    tol 1e-11, regular and pipelined schedules.  Too large for the oracle's Parareal, so:
+    converged Parareal equals serial fine stepping on the GPU (a property at any size), the
+    increments fall monotonically, and one step of the full system matches the oracle.
+
+    The pair sum sees the float64 state rounded to float32.  Here |X| reaches 10 against a node
+    spacing of 2e-3, and that rounding alone moves the oracle's own velocities by 1.3e-4 (u) /
+    7e-5 (omega), relative L2 (1.9e-6 for the 128-node rod near the origin).  So the velocities
+    of one Euler step, u = (X1 - X) / dt, are compared at 1e-5 with the oracle pair sum on the
+    rounded positions, and the RK2 step with the exact oracle at twice that floor."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(4, 8, 512)
+    gp, op = params(dict(W.ROD_PARAREAL), rs.eps)
+    dt = W.ROD_PARAREAL["dt"]
+    Ns, nf, r = 64, 16, 4
+    T1 = Ns * nf * dt
+    fresh = lambda: (torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda())
+    # one Euler step (all 4096 points): its velocities against the oracle's on the rounded state
+    X1, D1 = fresh()
+    mrs.rod_step(ctx, rs.rod_off, gp, X1, D1, 0.0, dt, 1, mrs.MRS_EULER)
+    g, m = orc.rod_forces(rs.rod_off, rs.X, rs.D, op, 0.0)
+    Xr = rs.X.astype(np.float32).astype(np.float64)
+    ur, _ = orc.mrs_velocity(Xr, g, m, rs.eps, 1.0)
+    assert rel((X1.cpu().numpy() - rs.X) / dt, ur) < 1e-5
+    # one fine RK2 step against the exact oracle
+    X1, D1 = fresh()
+    mrs.rod_step(ctx, rs.rod_off, gp, X1, D1, 0.0, dt, 1, mrs.MRS_RK2)
+    Xo, _ = orc.rod_step(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, 0.0, dt, 1, mrs.MRS_RK2)
+    assert rel(X1.cpu().numpy() - rs.X, Xo - rs.X) < 2.6e-4
+    # serial fine stepping over the whole horizon
+    Xs, Ds = fresh()
+    mrs.rod_step(ctx, rs.rod_off, gp, Xs, Ds, 0.0, dt, Ns * nf, mrs.MRS_RK2)
+    disp_s = Xs.cpu().numpy() - rs.X
+    Xp, Dp = fresh()
+    st = mrs.parareal_run(ctx, rs.rod_off, gp, Xp, Dp, 0.0, T1, Ns, dt, r, 8, 1e-11,
+                          group_size=group_size)
+    assert st.final_incr < 1e-11 and 2 <= st.iterations <= 8
+    inc = [st.incr[i] for i in range(st.iterations)]
+    assert all(b < a for a, b in zip(inc, inc[1:])), inc
+    assert rel(Xp.cpu().numpy() - rs.X, disp_s) < 1e-5
+    # frames stay orthonormal after the corrections
+    Dn = Dp.cpu().numpy()
+    eye = np.einsum("kij,klj->kil", Dn, Dn)
+    assert np.abs(eye - np.eye(3)).max() < 1e-10
