@@ -136,6 +136,16 @@ MRS_API int mrs_velocity(mrs_ctx* ctx, int n_sys, const int64_t* offsets,
                  void* u, void* w, double mu, double eps, const double* eps_per_sys,
                  int precision, void* stream);
 
+/* Builds and caches, without launching anything, the plan mrs_velocity uses for the shape
+ * (offsets, mu, eps or eps_per_sys, precision) -- its work table and scratch -- so that later
+ * mrs_velocity calls with that shape allocate nothing and may be captured in a CUDA graph.
+ * Call it off the hot path, once per shape; a shape already cached is only marked as the most
+ * recently used.  The context caches up to 16 shapes (the least recently used is evicted,
+ * after a device synchronisation, when a 17th is reserved or used).
+ * Arguments as for mrs_velocity.  Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */
+MRS_API int mrs_reserve(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
+                        const double* eps_per_sys, int precision);
+
 /* Pair sum that allocates nothing (the paper has no counterpart: this is a library service).
  * For callers that cannot call cudaMalloc -- code whose device memory belongs to another
  * allocator or a fixed budget, latency-critical loops that cannot pay for cudaMalloc's implicit

@@ -533,16 +533,15 @@ int mrs_plan_info(const mrs_plan* plan, int* grid, int64_t* work_units, int* con
     return MRS_OK;
 }
 
-int mrs_velocity(mrs_ctx* ctx, int n_sys, const int64_t* offsets, const void* X, const void* f,
-                 const void* n, const void* Xt, void* u, void* w, double mu, double eps,
-                 const double* eps_per_sys, int precision, void* stream)
+}  // extern "C"
+
+namespace mrs {
+
+// The context's cached plan for (offsets, eps, precision, mu), built and cached on a miss (the
+// least recently used plan is evicted beyond plan_cache_max).
+static int cached_plan(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
+                       const double* eps_per_sys, int precision, mrs_plan** out)
 {
-    clear_error();
-    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
-    int st = check_offsets(n_sys, offsets);
-    if (st) return st;
-    // look the shape up in the plan cache
-    mrs_plan* hit = nullptr;
     for (auto it = ctx->plan_cache.begin(); it != ctx->plan_cache.end(); ++it) {
         mrs_plan* p = *it;
         if (p->precision != precision || p->n_sys != n_sys || p->mu != mu) continue;
@@ -551,23 +550,51 @@ int mrs_velocity(mrs_ctx* ctx, int n_sys, const int64_t* offsets, const void* X,
         for (int s = 0; s < n_sys && same; ++s)
             same = p->eps[s] == (eps_per_sys ? eps_per_sys[s] : eps);
         if (!same) continue;
-        hit = p;
         ctx->plan_cache.erase(it);
-        ctx->plan_cache.push_front(hit);
-        break;
+        ctx->plan_cache.push_front(p);
+        *out = p;
+        return MRS_OK;
     }
-    if (!hit) {
-        st = plan_build(ctx, n_sys, offsets, mu, eps, eps_per_sys, precision, -1, &hit);
-        if (st) return st;
-        hit->owned_by_ctx = true;
-        ctx->plan_cache.push_front(hit);
-        while (ctx->plan_cache.size() > ctx->plan_cache_max) {  // evict the least recent
-            mrs_plan* old = ctx->plan_cache.back();
-            ctx->plan_cache.pop_back();
-            cudaDeviceSynchronize();   // the evicted plan's scratch may still be in use
-            plan_free(old);
-        }
+    mrs_plan* hit = nullptr;
+    const int st = plan_build(ctx, n_sys, offsets, mu, eps, eps_per_sys, precision, -1, &hit);
+    if (st) return st;
+    hit->owned_by_ctx = true;
+    ctx->plan_cache.push_front(hit);
+    while (ctx->plan_cache.size() > ctx->plan_cache_max) {  // evict the least recent
+        mrs_plan* old = ctx->plan_cache.back();
+        ctx->plan_cache.pop_back();
+        cudaDeviceSynchronize();   // the evicted plan's scratch may still be in use
+        plan_free(old);
     }
+    *out = hit;
+    return MRS_OK;
+}
+
+}  // namespace mrs
+
+extern "C" {
+
+int mrs_reserve(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
+                const double* eps_per_sys, int precision)
+{
+    clear_error();
+    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+    int st = check_offsets(n_sys, offsets);
+    if (st) return st;
+    mrs_plan* p = nullptr;
+    return cached_plan(ctx, n_sys, offsets, mu, eps, eps_per_sys, precision, &p);
+}
+
+int mrs_velocity(mrs_ctx* ctx, int n_sys, const int64_t* offsets, const void* X, const void* f,
+                 const void* n, const void* Xt, void* u, void* w, double mu, double eps,
+                 const double* eps_per_sys, int precision, void* stream)
+{
+    clear_error();
+    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+    int st = check_offsets(n_sys, offsets);
+    if (st) return st;
+    mrs_plan* hit = nullptr;
+    if ((st = cached_plan(ctx, n_sys, offsets, mu, eps, eps_per_sys, precision, &hit))) return st;
     MRS_CHECK_CUDA(cudaSetDevice(ctx->device));
     return plan_run(hit, X, f, n, Xt, u, w, (cudaStream_t)stream);
 }

@@ -35,6 +35,7 @@ EXPORTS = [
     "serve_cancel",
     "mrs_autotune", "mrs_autotune_save", "mrs_autotune_load", "parareal_run_pipelined",
     "rod_advance", "rod_checkpoint_save", "rod_checkpoint_load", "mrs_device_status",
+    "mrs_reserve",
 ]
 MRS_FLAG_NONFINITE = 1
 MRS_JOB_VELOCITY, MRS_JOB_ROD = 0, 1
@@ -114,6 +115,8 @@ def lib():
                                    ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _vp]
         L.mrs_plan_create.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_double, ctypes.c_double,
                                       _dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
+        L.mrs_reserve.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_double, ctypes.c_double, _dp,
+                                  ctypes.c_int]
         L.mrs_plan_execute.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.mrs_plan_destroy.argtypes = [_vp]
         L.mrs_plan_config_info.argtypes = [_vp, ctypes.c_int, _ip, _ip, _ip]
@@ -227,6 +230,18 @@ def mrs_velocity(ctx: Context, offsets, X, f, n, u, w, mu, eps, eps_per_sys=None
     _check(lib().mrs_velocity(ctx.handle, len(off) - 1, poff, _ptr(X), _ptr(f), _ptr(n), _ptr(Xt),
                               _ptr(u), _ptr(w), float(mu), float(eps), peps, int(precision),
                               _stream(stream)))
+
+
+def mrs_reserve(ctx: Context, offsets, mu, eps, eps_per_sys=None, precision=MRS_F32_COMP):
+    """``mrs_reserve``: build and cache the plan ``mrs_velocity`` uses for this shape, so that
+    later calls with it allocate nothing (and can be captured in a CUDA graph)."""
+    off, poff = _offsets(offsets)
+    peps = None
+    if eps_per_sys is not None:
+        eps_arr = np.ascontiguousarray(np.asarray(eps_per_sys, dtype=np.float64))
+        peps = eps_arr.ctypes.data_as(_dp)
+    _check(lib().mrs_reserve(ctx.handle, len(off) - 1, poff, float(mu), float(eps), peps,
+                             int(precision)))
 
 
 def mrs_velocity_noalloc(n_points, X, f, n, u, w, mu, eps, stream=None):

@@ -381,3 +381,40 @@ def test_nonfinite_inputs_raise_the_flag_through_the_symmetric_path(ctx):
     assert ctx.device_status() == 0
     assert not torch.isfinite(u).all()
     pl.close()
+
+
+def test_reserve_makes_mrs_velocity_allocation_free(ctx, orc):
+    """mrs_reserve builds the cached plan of a shape (its scratch shows up as device memory
+    taken); mrs_velocity on that shape then takes no device memory and can be captured in a
+    CUDA graph in global capture mode (which rejects allocation), and the replay matches the
+    eager call bit for bit and the oracle."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    p = W.single_system(seed=81, n_fil=4, M=1024)       # 4096 points: several MB of scratch
+    mu, eps = 1.7, float(p.eps[0])                      # a shape no other test caches
+    X, f, n = dev(p.X), dev(p.f), dev(p.n)
+    ue, we = torch.empty_like(X), torch.empty_like(X)
+    u, w = torch.full_like(X, float("nan")), torch.full_like(X, float("nan"))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    mrs.mrs_reserve(ctx, p.offsets, mu, eps)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 < free0
+    mrs.mrs_velocity(ctx, p.offsets, X, f, n, ue, we, mu, eps)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free1
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side, capture_error_mode="global"):
+            mrs.mrs_velocity(ctx, p.offsets, X, f, n, u, w, mu, eps, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(u, ue) and torch.equal(w, we)
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, eps, mu)
+    assert rel_l2(u.cpu().numpy(), ur) < TOL32 and rel_l2(w.cpu().numpy(), wr) < TOL32
+    mrs.mrs_reserve(ctx, p.offsets, mu, eps)             # already cached: nothing new
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free1
