@@ -476,9 +476,7 @@ static int occ_sym_t(int* n)
 // source's kernel values while accumulating the current one's (software pipelining, 2 packs,
 // 200 registers) was slower: 1.74 ms; unrolling 25's source loop twice changed nothing (1.612);
 // keeping the tile's f and n in shared memory (126 registers, 16 warps per SM, 64-source
-// chunks) was slower too: 1.68 ms at 4 points per thread, 1.64 ms at 6; so was more occupancy
-// through a register cap (25 held to 168 registers, no spills, 6 CTAs of 64 threads per SM:
-// 1.624 ms; 64 threads x 4 points at 6 CTAs per SM: 1.634 ms).
+// chunks) was slower too: 1.68 ms at 4 points per thread, 1.64 ms at 6.
 #define MRS_SYM_DISPATCH(cfg, comp, FN, ...)                             \
     switch (cfg) {                                                       \
         MRS_SYM_CASE(17, 128, 4, false, false, FN, __VA_ARGS__)          \
