@@ -183,3 +183,44 @@ def test_cancel_waiting_job(ctx):
         assert srv.poll(t_long)[0]
     finally:
         srv.close()
+
+
+def test_served_rod_job_with_lennard_jones(ctx):
+    """A served rod job with the Lennard-Jones repulsion (two parallel rods 0.12 apart, inside
+    the cut-off) reaches the state rod_step reaches (the fused one-launch solve and the per-step
+    kernel graphs), and the repulsion changes its motion."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    M = 40
+    X1, D1 = W.sinusoid_filament(M)
+    X = np.concatenate([X1, X1 + np.array([0.0, 0.0, 0.12])])
+    D = np.concatenate([D1, D1])
+    off = np.array([0, M, 2 * M], np.int64)
+    eps = 1.5 / (M - 1)
+    c = dict(W.ROD_PLAIN, a=(2e-3,) * 3, b=(20.0,) * 3)
+    out = {}
+    for lj in (0.0, 0.05):
+        prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"],
+                                 1.0, eps, lj_eps=lj)
+        srv = mrs.Server(ctx, 1 << 28, 8)
+        try:
+            Xs, Ds = torch.from_numpy(X.copy()).cuda(), torch.from_numpy(D.copy()).cuda()
+            t = srv.submit_rod(off, Xs, Ds, prm, 0.0, 2e-6, 60, mrs.MRS_RK2, 1.0, eps)
+            srv.drain()
+            assert srv.poll(t)[0]
+            out[(lj, "serve")] = Xs.cpu().numpy()
+        finally:
+            srv.close()
+        try:
+            for fused in (1, 0):
+                ctx.set_fused_steps(fused)
+                Xd, Dd = torch.from_numpy(X.copy()).cuda(), torch.from_numpy(D.copy()).cuda()
+                mrs.rod_step(ctx, off, prm, Xd, Dd, 0.0, 2e-6, 60, mrs.MRS_RK2)
+                torch.cuda.synchronize()
+                out[(lj, fused)] = Xd.cpu().numpy()
+        finally:
+            ctx.set_fused_steps(1)
+    for lj in (0.0, 0.05):
+        ref = out[(lj, 0)] - X
+        assert rel(out[(lj, "serve")] - X, ref) < 1e-5
+        assert rel(out[(lj, 1)] - X, ref) < 1e-5
+    assert rel(out[(0.05, "serve")] - X, out[(0.0, "serve")] - X) > 1e-3
