@@ -257,3 +257,67 @@ def test_two_point_brute_force_matches_superposition(orc):
         ws += b
     np.testing.assert_allclose(u, us, rtol=1e-12, atol=1e-12 * np.abs(u).max())
     np.testing.assert_allclose(w, ws, rtol=1e-12, atol=1e-12 * np.abs(w).max())
+
+
+def _symbolic_fields():
+    """The paper's regularized Stokeslet (H1, H2 of its cited source) and blob, Section II-C;
+    the other three couplings derived from it: the velocity of a point torque n is
+    (1/2) curl of the Stokeslet of n, and omega = (1/2) curl u (Eq. angular_velocity_field).
+    Returns the symbols and u_f, omega_f, u_n, omega_n, the Stokes residual and div u."""
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z", real=True)
+    e = sp.symbols("epsilon", positive=True)
+    f = sp.Matrix(sp.symbols("f1:4", real=True))
+    n = sp.Matrix(sp.symbols("n1:4", real=True))
+    X = sp.Matrix([x, y, z])
+    r2 = x**2 + y**2 + z**2
+    d = r2 + e**2
+    H1 = (r2 + 2 * e**2) / (8 * sp.pi * d**sp.Rational(3, 2))
+    H2 = 1 / (8 * sp.pi * d**sp.Rational(3, 2))
+    phi = 15 * e**4 / (8 * sp.pi * d**sp.Rational(7, 2))
+    stokeslet = lambda F: F * H1 + F.dot(X) * X * H2
+    pressure = lambda F: F.dot(X) * (2 * r2 + 5 * e**2) / (8 * sp.pi * d**sp.Rational(5, 2))
+    grad = lambda s: sp.Matrix([sp.diff(s, c) for c in (x, y, z)])
+    lap = lambda v: sp.Matrix([sum(sp.diff(v[i], c, 2) for c in (x, y, z)) for i in range(3)])
+    curl = lambda v: sp.Matrix([sp.diff(v[2], y) - sp.diff(v[1], z),
+                                sp.diff(v[0], z) - sp.diff(v[2], x),
+                                sp.diff(v[1], x) - sp.diff(v[0], y)])
+    u_f = stokeslet(f)
+    resid = lap(u_f) - grad(pressure(f)) + f * phi           # mu = 1
+    div = sum(sp.diff(u_f[i], c) for i, c in enumerate((x, y, z)))
+    u_n = curl(stokeslet(n)) / 2
+    return sp, (x, y, z, e, f, n, d), u_f, curl(u_f) / 2, u_n, curl(u_n) / 2, resid, div
+
+
+def test_symbolic_stokes_residual_and_divergence():
+    """Pin (i): the Stokeslet with the paper's blob as forcing solves the regularized Stokes
+    equations mu Lap u - grad p + f phi_eps = 0 and div u = 0 exactly (symbolic algebra)."""
+    sp, (x, y, z, e, f, n, d), *_, resid, div = _symbolic_fields()
+    for c in resid:
+        assert sp.simplify(c * d**sp.Rational(9, 2)) == 0
+    assert sp.simplify(div) == 0
+
+
+@pytest.mark.parametrize("point", [("0", "0", "0"), ("1/3", "1/5", "-1/7"), ("1", "2", "-3"),
+                                   ("25/2", "-9", "31/4")])
+def test_two_point_case_exact(orc, point):
+    """Pin (vii): one source at the origin with rational f, n and eps, one target at a rational
+    point (at the source, at a few eps, in the far field), mu = 7/3; the oracle's four
+    couplings match the symbolically derived fields evaluated to 30 digits, divided by mu."""
+    sp, (x, y, z, e, f, n, d), u_f, w_f, u_n, w_n, *_ = _symbolic_fields()
+    eps = sp.Rational(1, 10)
+    fv = [sp.Rational(1), sp.Rational(-2), sp.Rational(3, 2)]
+    nv = [sp.Rational(-1, 2), sp.Rational(1), sp.Rational(2)]
+    pt = [sp.Rational(str(c)) for c in point]
+    subs = {x: pt[0], y: pt[1], z: pt[2], e: eps}
+    subs.update({f[i]: fv[i] for i in range(3)})
+    subs.update({n[i]: nv[i] for i in range(3)})
+    exact = lambda v: np.array([float(sp.N(c.subs(subs), 30)) for c in v])
+    mu = 7.0 / 3.0
+    u_ref = (exact(u_f) + exact(u_n)) / mu
+    w_ref = (exact(w_f) + exact(w_n)) / mu
+    xt = np.array([[float(c) for c in pt]])
+    u, w = orc.mrs_velocity(np.zeros((1, 3)), np.array([[float(c) for c in fv]]),
+                            np.array([[float(c) for c in nv]]), 0.1, mu, xt=xt)
+    assert np.abs(u[0] - u_ref).max() <= 1e-14 * np.abs(u_ref).max()
+    assert np.abs(w[0] - w_ref).max() <= 1e-14 * np.abs(w_ref).max()

@@ -28,6 +28,7 @@ MRS_PINS = [
     lambda o: TM.test_self_term_closed_form(o),
     lambda o: TM.test_mobility_symmetric_psd(o, "rod", 1.5),
     lambda o: TM.test_equivariances(o),
+    lambda o: TM.test_two_point_case_exact(o, ("1/3", "1/5", "-1/7")),
 ]
 
 MRS_MUTANTS = {
