@@ -57,6 +57,7 @@ ROD_PINS = [
     lambda o: TR.test_force_is_minus_energy_gradient(o),
     lambda o: TR.test_torque_is_minus_energy_rotation_derivative(o),
     lambda o: TR.test_total_force_and_torque_vanish(o),
+    lambda o: TR.test_initial_sinusoid_forces_vanish_at_second_order(o),
     lambda o: TR.test_objectivity(o),
     lambda o: TR.test_energy_decreases_under_euler_flow(o),
     lambda o: TR.test_convergence_order(o, 1, 2),

@@ -113,6 +113,29 @@ def test_straight_unstressed_rod_is_force_free(orc):
     assert np.abs(g).max() < 1e-13 and np.abs(m).max() < 1e-13
 
 
+def test_initial_sinusoid_forces_vanish_at_second_order(orc):
+    """The initial configuration (reading R6): nodes evenly spaced in arclength on the unit
+    sinusoid, D3 its tangent.  Shear and stretch then vanish up to the midpoint rule's O(ds^2)
+    error, so the point forces g_k = -f_k ds shrink like ds^2 at the free ends and like ds^3
+    inside (force densities O(ds^2)) under refinement.  The forces do not depend on the
+    preferred curvature, so this holds at any time."""
+    p = params(orc, a=0.02, b=140.0)
+    g_in, g_all = [], []
+    for M in (65, 129, 257):
+        X, D = W.sinusoid_filament(M)
+        for t in (0.0, 0.1):
+            g, _ = orc.rod_forces([0, M], X, D, p, t)
+            if t == 0.0:
+                g_in.append(np.abs(g[1:-1]).max())
+                g_all.append(np.abs(g).max())
+            else:
+                assert np.array_equal(np.abs(g).max(), g_all[-1])
+    for a, b in zip(g_in, g_in[1:]):
+        assert math.log2(a / b) > 2.8, g_in
+    for a, b in zip(g_all, g_all[1:]):
+        assert math.log2(a / b) > 1.8, g_all
+
+
 def test_objectivity(orc):
     X, D = perturbed_rod(25, 43)
     p = params(orc, a=0.3, b=2.0)
