@@ -418,3 +418,57 @@ def test_reserve_makes_mrs_velocity_allocation_free(ctx, orc):
     mrs.mrs_reserve(ctx, p.offsets, mu, eps)             # already cached: nothing new
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free1
+
+
+def degenerate_system():
+    """One system with the method's degenerate geometries: points repeated exactly (r = 0
+    between distinct points), a cluster within 1e-3 eps, and clusters 1e4 eps apart."""
+    from paper_2604_12083_gb300 import workloads as W
+    rng = np.random.default_rng(84)
+    eps = float(np.float32(0.01))
+    base = rng.uniform(0.0, 1.0, (300, 3))
+    dup = base[:100].copy()                                  # exact repeats
+    tight = base[200] + rng.uniform(-1e-5, 1e-5, (60, 3))    # within 1e-3 eps
+    far = rng.uniform(0.0, 1.0, (77, 3)) + 100.0             # 1e4 eps away
+    X = np.concatenate([base, dup, tight, far]).astype(np.float32)
+    f = rng.standard_normal(X.shape).astype(np.float32)
+    n = rng.standard_normal(X.shape).astype(np.float32)
+    off = np.array([0, X.shape[0]], np.int64)
+    return W.MRSProblem("degenerate", off, X, f, n, np.array([eps]), 1.0)
+
+
+@pytest.mark.parametrize("config", [None, 8, 14, 25])
+def test_degenerate_geometries(ctx, orc, config):
+    from paper_2604_12083_gb300 import mrs
+    p = degenerate_system()
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+    for prec in (mrs.MRS_F32, mrs.MRS_F32_COMP):
+        u, w = run(ctx, p, prec, config=config)
+        assert np.isfinite(u).all() and np.isfinite(w).all()
+        assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
+    u, w = run(ctx, p, mrs.MRS_F64)
+    assert rel_l2(u, ur) < TOL64 and rel_l2(w, wr) < TOL64
+
+
+def test_single_point_closed_form_and_zero_sources(ctx):
+    """A lone point: u = f / (4 pi mu eps), omega = 5 n / (16 pi mu eps^3) (the r = 0 values of
+    H1 and H4), in every precision; zero forces and torques give exactly zero."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    eps, mu = 0.05, 1.3
+    f = np.array([[0.5, -1.0, 2.0]])
+    n = np.array([[1.5, 0.25, -0.75]])
+    X = np.array([[3.0, -2.0, 1.0]])
+    p = W.MRSProblem("lone", np.array([0, 1], np.int64), X.astype(np.float32),
+                     f.astype(np.float32), n.astype(np.float32), np.array([eps]), mu)
+    u_ref = f / (4 * np.pi * mu * eps)
+    w_ref = 5 * n / (16 * np.pi * mu * eps**3)
+    for prec, tol in ((mrs.MRS_F32, 1e-6), (mrs.MRS_F32_COMP, 1e-6), (mrs.MRS_F64, 1e-14)):
+        u, w = run(ctx, p, prec)
+        assert rel_l2(u, u_ref) < tol and rel_l2(w, w_ref) < tol
+    z = W.MRSProblem("zero", np.array([0, 700], np.int64),
+                     np.random.default_rng(85).uniform(0, 1, (700, 3)).astype(np.float32),
+                     np.zeros((700, 3), np.float32), np.zeros((700, 3), np.float32),
+                     np.array([eps]), mu)
+    for config in (None, 8, 25):
+        u, w = run(ctx, z, mrs.MRS_F32_COMP, config=config)
+        assert not u.any() and not w.any()
