@@ -440,3 +440,43 @@ def test_parareal_full_size_workload(ctx, orc, group_size):
     Dn = Dp.cpu().numpy()
     eye = np.einsum("kij,klj->kil", Dn, Dn)
     assert np.abs(eye - np.eye(3)).max() < 1e-10
+
+
+def test_ragged_rod_batch(ctx, orc):
+    """Unit rods of 2, 3, 5, 127, 128, 129, 255 and 300 nodes in one call (node spacings from 1
+    to 1/299, around the fused force kernel's chunks of 127 nodes): rod_forces against the
+    oracle, and 30 RK2 steps on both stepping paths (fused launch, kernel graphs) against the
+    oracle's."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    sizes = [2, 3, 5, 127, 128, 129, 255, 300]
+    rng = np.random.default_rng(86)
+    Xs, Ds = [], []
+    for M in sizes:
+        X, D = W.sinusoid_filament(M)
+        Q = np.linalg.qr(rng.standard_normal((3, 3)))[0]
+        Q *= np.sign(np.linalg.det(Q))
+        Xs.append(X @ Q.T + rng.uniform(0.0, 2.0, 3))
+        Ds.append(np.einsum("rc,kic->kir", Q, D))
+    X = np.concatenate(Xs)
+    D = np.concatenate(Ds)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    eps = 1.5 / 299.0
+    cfg = dict(W.ROD_PLAIN, a=(2e-3,) * 3, b=(20.0,) * 3)
+    gp, op = params(cfg, eps)
+    Xd, Dd = torch.from_numpy(X).cuda(), torch.from_numpy(D).cuda()
+    g, m = torch.empty_like(Xd), torch.empty_like(Xd)
+    mrs.rod_forces(ctx, off, gp, Xd, Dd, 0.3, g, m)
+    go, mo = orc.rod_forces(off, X, D, op, 0.3)
+    assert np.abs(g.cpu().numpy() - go).max() <= 1e-11 * np.abs(go).max()
+    assert np.abs(m.cpu().numpy() - mo).max() <= 1e-11 * np.abs(mo).max()
+    dt = 2e-7                               # resolves the stiffest mode of the 300-node rod
+    Xo, _ = orc.rod_step(off, X, D, op, eps, 1.0, 0.0, dt, 30, mrs.MRS_RK2)
+    try:
+        for fused in (1, 0):
+            ctx.set_fused_steps(fused)
+            Xs_, Ds_ = torch.from_numpy(X.copy()).cuda(), torch.from_numpy(D.copy()).cuda()
+            mrs.rod_step(ctx, off, gp, Xs_, Ds_, 0.0, dt, 30, mrs.MRS_RK2)
+            torch.cuda.synchronize()
+            assert rel(Xs_.cpu().numpy() - X, Xo - X) < 1e-4, fused
+    finally:
+        ctx.set_fused_steps(1)
