@@ -252,7 +252,10 @@ MRS_API int rod_advance(mrs_ctx* ctx, int64_t N, double* X, double* D, const voi
 /* nsteps explicit time steps of all rods as ONE hydrodynamic system (every node is a source
  * for every node), in place on device float64 X[N][3], D[N][3][3], from time t0 with step dt.
  * Each stage: rod_forces -> float32 pack -> MRS pair sum (mrs_precision) -> float64 update
- * (Eq. newx; Eq. newD Rodrigues rotation of the frame by |omega| dt about omega).
+ * (Eq. newx; Eq. newD Rodrigues rotation of the frame by |omega| dt about omega).  The float32
+ * packs hold positions relative to a reference point of the current state (the mean of the
+ * middle nodes of up to 8 rods), so the pair sum's accuracy does not depend on where the
+ * system sits; results do not depend on how a run is split into calls.
  * scheme MRS_EULER or MRS_RK2 (explicit midpoint on positions and frames).  The steps are
  * captured once into a CUDA graph per (rods, scheme) and replayed.  Synchronizes `stream`
  * only at set-up.  Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */

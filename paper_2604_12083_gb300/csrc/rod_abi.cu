@@ -163,6 +163,7 @@ RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt)
     L.chunks = ws->d_chunks;
     L.n_chunks = ws->n_chunks;
     L.inv_L = 1.0 / p->L;
+    set_pack_reference(L, ws->n_rods, ws->rod_off.data());
     return L;
 }
 

@@ -17,7 +17,26 @@ struct RodLaunch {
     const int* chunks;         // [n_chunks] base node of every fused-kernel chunk, or NULL
     int n_chunks;
     double inv_L;              // 1 / p.L
+    // Reference point of the float32 position packs (see rod_kernels.cu): the mean of the
+    // nodes ref[0..n_ref) of the instance (indices within it), weight ref_w = 1 / n_ref;
+    // n_ref = 0 packs X itself.
+    int n_ref;
+    int ref[8];
+    double ref_w;
 };
+
+// The reference nodes of an instance with rods rod_off[0..n_rods]: the middle node of up to 8
+// rods spread over it (a function of the rod layout only).
+inline void set_pack_reference(RodLaunch& L, int n_rods, const int64_t* rod_off)
+{
+    const int R = n_rods < 8 ? n_rods : 8;
+    L.n_ref = R;
+    for (int i = 0; i < R; ++i) {
+        const int r = (int)((long long)i * n_rods / R);
+        L.ref[i] = (int)(rod_off[r] + (rod_off[r + 1] - rod_off[r] - 1) / 2);
+    }
+    L.ref_w = R > 0 ? 1.0 / R : 0.0;
+}
 constexpr int kRodChunk = 128;   // threads per fused rod-force CTA (kRodChunk - 1 nodes each)
 
 cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double* D, double t_off,

@@ -172,7 +172,7 @@ __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__
 // float32 copies (X, g, m) the pair sum reads when Xf is given.
 __device__ __forceinline__ void node_fn(const double* __restrict__ X, long long k, const double* fp,
                                         const double* fm, double* g64, double* m64, float* Xf,
-                                        float* gf, float* mf)
+                                        float* gf, float* mf, const double* ref = nullptr)
 {
     const double* Xk = X + 3 * (size_t)k;
     double g[3] = {0, 0, 0}, m[3] = {0, 0, 0};
@@ -201,11 +201,34 @@ __device__ __forceinline__ void node_fn(const double* __restrict__ X, long long 
             m64[3 * (size_t)k + c] = m[c];
         }
         if (Xf) {
-            Xf[3 * (size_t)k + c] = (float)Xk[c];
+            Xf[3 * (size_t)k + c] = (float)(ref ? Xk[c] - ref[c] : Xk[c]);
             gf[3 * (size_t)k + c] = (float)g[c];
             mf[3 * (size_t)k + c] = (float)m[c];
         }
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Reference point of the float32 position packs.  The pair sum depends on differences of
+// positions only, but rounding X to float32 moves every separation by up to |X| 2^-24, which
+// against a node spacing ds is a relative error |X| 2^-24 / ds in the near-field kernels.  So the
+// packs hold X - c, c the mean of a few fixed nodes of the instance (the middle node of up to 8
+// rods spread over it, RodLaunch::ref) in the state being packed: a function of that state
+// alone, summed in a fixed order, so every path packs the same values and how a run is split
+// into calls does not change its rounding.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void pack_reference(const RodLaunch& L, const double* Xinst, double* c)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < L.n_ref; ++i) {
+        const double* x = Xinst + 3 * L.ref[i];
+        s0 += x[0];
+        s1 += x[1];
+        s2 += x[2];
+    }
+    c[0] = s0 * L.ref_w;
+    c[1] = s1 * L.ref_w;
+    c[2] = s2 * L.ref_w;
 }
 
 __global__ void rod_node_kernel(const RodLaunch L, const double* __restrict__ X, double* g64,
@@ -214,8 +237,12 @@ __global__ void rod_node_kernel(const RodLaunch L, const double* __restrict__ X,
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.N) return;
     const int2 ni = L.node_info[k];
+    double ref[3];
+    const bool centred = Xf && L.n_ref > 0;
+    if (centred) pack_reference(L, X + 3 * (size_t)(k / L.nodes_per_inst) * L.nodes_per_inst, ref);
     node_fn(X, k, ni.x < ni.y - 1 ? L.FN + 6 * (size_t)k : nullptr,
-            ni.x > 0 ? L.FN + 6 * (size_t)(k - 1) : nullptr, g64, m64, Xf, gf, mf);
+            ni.x > 0 ? L.FN + 6 * (size_t)(k - 1) : nullptr, g64, m64, Xf, gf, mf,
+            centred ? ref : nullptr);
 }
 
 // Both steps in one launch.  A CTA covers kRodChunk - 1 consecutive nodes of one rod: thread t
@@ -228,16 +255,19 @@ __global__ void __launch_bounds__(kRodChunk) rod_forces_fused_kernel(
     double* g64, double* m64, float* Xf, float* gf, float* mf)
 {
     __shared__ double sFN[kRodChunk * 6];
+    __shared__ double sref[3];
     const long long k0 = L.chunks[blockIdx.x];
     const int2 ni0 = L.node_info[k0];
     const int M = ni0.y, t = threadIdx.x;
     const int s = ni0.x - 1 + t;   // segment index within the rod
+    const bool centred = Xf && L.n_ref > 0;   // a chunk lies in one rod, hence in one instance
+    if (centred && t == 0) pack_reference(L, X + 3 * (size_t)(k0 / L.nodes_per_inst) * L.nodes_per_inst, sref);
     if (s >= 0 && s < M - 1) segment_fn(L, X, D, t_off, k0 - 1 + t, s, M, sFN + 6 * t);
     __syncthreads();
     const int n = ni0.x + t - 1;   // node index within the rod
     if (t == 0 || n >= M) return;
     node_fn(X, k0 + t - 1, n < M - 1 ? sFN + 6 * t : nullptr, n > 0 ? sFN + 6 * (t - 1) : nullptr,
-            g64, m64, Xf, gf, mf);
+            g64, m64, Xf, gf, mf, centred ? sref : nullptr);
 }
 
 // Eq. (newD): rotate the three directors of node k by |w| h about w / |w| (unchanged if w = 0),
@@ -339,13 +369,17 @@ __device__ __forceinline__ void fused_kahan(float& sum, float& comp, float v)
 // Omega_2 = -k_w^2 A (sin(k_w s_mid) cos(f t) + cos(k_w s_mid) sin(f t)) needs one sincos per
 // stage (one thread, shared through stime) instead of one sin per segment.
 template <int BLOCK>
-__device__ void fused_velocity(const mrs_rod_params& P, const FusedConst& K, int N1,
+__device__ void fused_velocity(const RodLaunch& L, const FusedConst& K, int N1,
                                const int2* sni, const double* sseg, const double* sXs,
-                               const double* sDs, double t, double* stime, double* sFN,
-                               float* sXf, float* sgf, float* smf, float* su, float* sw)
+                               const double* sDs, double t, double* stime, double* sref,
+                               double* sFN, float* sXf, float* sgf, float* smf, float* su, float* sw)
 {
+    const mrs_rod_params& P = L.p;
     const int tid = threadIdx.x;
-    if (tid == 0) sincos(P.wave_f * t, &stime[0], &stime[1]);
+    if (tid == 0) {
+        sincos(P.wave_f * t, &stime[0], &stime[1]);
+        pack_reference(L, sXs, sref);   // reference point of this stage's float32 packs
+    }
     __syncthreads();
     const double sft = stime[0], cft = stime[1];
     const double amp = -P.wave_k * P.wave_k * P.wave_A;
@@ -360,7 +394,7 @@ __device__ void fused_velocity(const mrs_rod_params& P, const FusedConst& K, int
     for (int k = tid; k < N1; k += BLOCK) {
         const int2 ni = sni[k];
         node_fn(sXs, k, ni.x < ni.y - 1 ? sFN + 6 * k : nullptr, ni.x > 0 ? sFN + 6 * (k - 1) : nullptr,
-                nullptr, nullptr, sXf, sgf, smf);
+                nullptr, nullptr, sXf, sgf, smf, sref);
     }
     __syncthreads();
     if (P.lj_eps > 0.0) {
@@ -474,7 +508,8 @@ __global__ void __launch_bounds__(BLOCK) rod_fine_fused_kernel(const RodLaunch L
     double* sFN = sDh + 9 * N1;
     double* sseg = sFN + 6 * N1;
     double* stime = sseg + 3 * N1;   // sin(f t), cos(f t) of the current stage
-    int2* sni = reinterpret_cast<int2*>(stime + 2);
+    double* sref = stime + 2;        // reference point of the current stage's float32 packs
+    int2* sni = reinterpret_cast<int2*>(sref + 3);
     float* sXf = reinterpret_cast<float*>(sni + N1);
     float* sgf = sXf + 3 * N1;
     float* smf = sgf + 3 * N1;
@@ -498,13 +533,13 @@ __global__ void __launch_bounds__(BLOCK) rod_fine_fused_kernel(const RodLaunch L
     __syncthreads();
     for (int st = 0; st < nsteps; ++st) {
         const double t = t0 + (double)st * L.dt;
-        fused_velocity<BLOCK>(L.p, K, N1, sni, sseg, sX, sD, t, stime, sFN, sXf, sgf, smf, su, sw);
+        fused_velocity<BLOCK>(L, K, N1, sni, sseg, sX, sD, t, stime, sref, sFN, sXf, sgf, smf, su, sw);
         if (scheme == MRS_EULER) {
             fused_update<BLOCK>(N1, sX, sD, su, sw, L.dt, sX, sD);
         } else {
             fused_update<BLOCK>(N1, sX, sD, su, sw, 0.5 * L.dt, sXh, sDh);
-            fused_velocity<BLOCK>(L.p, K, N1, sni, sseg, sXh, sDh, t + 0.5 * L.dt, stime, sFN, sXf,
-                                  sgf, smf, su, sw);
+            fused_velocity<BLOCK>(L, K, N1, sni, sseg, sXh, sDh, t + 0.5 * L.dt, stime, sref, sFN,
+                                  sXf, sgf, smf, su, sw);
             fused_update<BLOCK>(N1, sX, sD, su, sw, L.dt, sX, sD);
         }
     }
@@ -518,7 +553,7 @@ constexpr int kFusedBlock = 256;
 
 size_t fused_smem_bytes(int N1)
 {
-    return 2 * sizeof(double) + (size_t)N1 * (33 * sizeof(double) + sizeof(int2) + 15 * sizeof(float));
+    return 5 * sizeof(double) + (size_t)N1 * (33 * sizeof(double) + sizeof(int2) + 15 * sizeof(float));
 }
 
 bool fused_fits(int N1)

@@ -295,6 +295,7 @@ cudaError_t admit_enqueue(mrs_server* S, SJob* j)
     L.chunks = nullptr;   // two-kernel force path (no chunk table in the pool)
     L.n_chunks = 0;
     L.inv_L = 1.0 / J.params.L;
+    set_pack_reference(L, J.n_rods, j->rod_off.data());
     return cudaSuccess;
 }
 

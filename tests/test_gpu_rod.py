@@ -401,11 +401,12 @@ def test_parareal_full_size_workload(ctx, orc, group_size):
     converged Parareal equals serial fine stepping on the GPU (a property at any size), the
     increments fall monotonically, and one step of the full system matches the oracle.
 
-    The pair sum sees the float64 state rounded to float32.  Here |X| reaches 10 against a node
-    spacing of 2e-3, and that rounding alone moves the oracle's own velocities by 1.3e-4 (u) /
-    7e-5 (omega), relative L2 (1.9e-6 for the 128-node rod near the origin).  So the velocities
-    of one Euler step, u = (X1 - X) / dt, are compared at 1e-5 with the oracle pair sum on the
-    rounded positions, and the RK2 step with the exact oracle at twice that floor."""
+    The pair sum sees the float64 state rounded to float32, relative to a reference point c,
+    the mean of the middle nodes of the 8 rods; with |X - c| up to ~6 against a node spacing of
+    2e-3 that rounding alone moves the oracle's own velocities by 3.5e-5, relative L2 (1.3e-4
+    if rounded without c).  So the velocities of one Euler step, u = (X1 - X) / dt, are compared at 1e-5
+    with the oracle pair sum on the same rounded positions, and the RK2 step with the exact
+    oracle at 1e-4."""
     from paper_2604_12083_gb300 import mrs, workloads as W
     rs = W.rod_system(4, 8, 512)
     gp, op = params(dict(W.ROD_PARAREAL), rs.eps)
@@ -417,14 +418,16 @@ def test_parareal_full_size_workload(ctx, orc, group_size):
     X1, D1 = fresh()
     mrs.rod_step(ctx, rs.rod_off, gp, X1, D1, 0.0, dt, 1, mrs.MRS_EULER)
     g, m = orc.rod_forces(rs.rod_off, rs.X, rs.D, op, 0.0)
-    Xr = rs.X.astype(np.float32).astype(np.float64)
+    mid = [rs.rod_off[r] + (rs.rod_off[r + 1] - rs.rod_off[r] - 1) // 2 for r in range(8)]
+    c = rs.X[mid].sum(axis=0) * (1.0 / 8)
+    Xr = (rs.X - c).astype(np.float32).astype(np.float64)
     ur, _ = orc.mrs_velocity(Xr, g, m, rs.eps, 1.0)
     assert rel((X1.cpu().numpy() - rs.X) / dt, ur) < 1e-5
     # one fine RK2 step against the exact oracle
     X1, D1 = fresh()
     mrs.rod_step(ctx, rs.rod_off, gp, X1, D1, 0.0, dt, 1, mrs.MRS_RK2)
     Xo, _ = orc.rod_step(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, 0.0, dt, 1, mrs.MRS_RK2)
-    assert rel(X1.cpu().numpy() - rs.X, Xo - rs.X) < 2.6e-4
+    assert rel(X1.cpu().numpy() - rs.X, Xo - rs.X) < 1e-4
     # serial fine stepping over the whole horizon
     Xs, Ds = fresh()
     mrs.rod_step(ctx, rs.rod_off, gp, Xs, Ds, 0.0, dt, Ns * nf, mrs.MRS_RK2)
@@ -478,5 +481,34 @@ def test_ragged_rod_batch(ctx, orc):
             mrs.rod_step(ctx, off, gp, Xs_, Ds_, 0.0, dt, 30, mrs.MRS_RK2)
             torch.cuda.synchronize()
             assert rel(Xs_.cpu().numpy() - X, Xo - X) < 1e-4, fused
+    finally:
+        ctx.set_fused_steps(1)
+
+
+def test_rod_far_from_the_origin(ctx, orc):
+    """The plain 128-node rod moved to (1000, -500, 250): packing float32 positions relative to
+    the rod's middle node keeps the pair sum as accurate as at the origin (rounded as they
+    are, positions near 1000 would move near-neighbour separations by 1000 2^-24 / ds ~ 8e-3
+    relative).  200 RK2 steps on both stepping paths against the oracle, and against the same
+    rod stepped at the origin."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(1, 1, 128)
+    shift = np.array([1000.0, -500.0, 250.0])
+    gp, op = params(dict(W.ROD_PLAIN), rs.eps)
+    dt = W.ROD_PLAIN["dt"]
+    Xo, _ = orc.rod_step(rs.rod_off, rs.X + shift, rs.D, op, rs.eps, 1.0, 0.0, dt, 200, mrs.MRS_RK2)
+    disp_o = Xo - (rs.X + shift)
+    try:
+        for fused in (1, 0):
+            ctx.set_fused_steps(fused)
+            out = []
+            for sh in (shift, np.zeros(3)):
+                Xd = torch.from_numpy(rs.X + sh).cuda()
+                Dd = torch.from_numpy(rs.D.copy()).cuda()
+                mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, 0.0, dt, 200, mrs.MRS_RK2)
+                torch.cuda.synchronize()
+                out.append(Xd.cpu().numpy() - (rs.X + sh))
+            assert rel(out[0], disp_o) < 1e-4, fused
+            assert rel(out[0], out[1]) < 1e-5, fused
     finally:
         ctx.set_fused_steps(1)
