@@ -376,10 +376,9 @@ __device__ void fused_velocity(const RodLaunch& L, const FusedConst& K, int N1,
 {
     const mrs_rod_params& P = L.p;
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        sincos(P.wave_f * t, &stime[0], &stime[1]);
-        pack_reference(L, sXs, sref);   // reference point of this stage's float32 packs
-    }
+    static_assert(BLOCK > 32, "the reference point is taken by a thread of the second warp");
+    if (tid == 0) sincos(P.wave_f * t, &stime[0], &stime[1]);
+    if (tid == 32) pack_reference(L, sXs, sref);   // reference point of this stage's float32 packs
     __syncthreads();
     const double sft = stime[0], cft = stime[1];
     const double amp = -P.wave_k * P.wave_k * P.wave_A;
