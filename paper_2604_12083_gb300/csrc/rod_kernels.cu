@@ -25,11 +25,12 @@ __device__ __forceinline__ double dot3(const double* a, const double* b)
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
-// Unit quaternion (w, x, y, z) of a rotation matrix A (row-major), w >= 0.
+// Quaternion (w, x, y, z) of a rotation matrix A (row-major), w >= 0, of unit length up to the
+// rounding of A (not normalised: its one user normalises the half-angle quaternion instead).
 __device__ __forceinline__ void rot_to_quat(const double* A, double* q)
 {
     // each branch: r = sqrt(x) and 1/(2r) from one reciprocal square root (x >= 1 on the
-    // branch taken, so no zero division), q scaled to unit length at the end
+    // branch taken, so no zero division)
     const double tr = A[0] + A[4] + A[8];
     if (tr >= A[0] && tr >= A[4] && tr >= A[8]) {
         const double x = fmax(1.0 + tr, 0.0), ir = rsqrt(x);
@@ -66,11 +67,6 @@ __device__ __forceinline__ void rot_to_quat(const double* A, double* q)
         q[2] = -q[2];
         q[3] = -q[3];
     }
-    const double nn = rsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    q[0] *= nn;
-    q[1] *= nn;
-    q[2] *= nn;
-    q[3] *= nn;
 }
 
 // Rotation matrix (row-major) of the principal square root of the rotation A.
@@ -78,9 +74,12 @@ __device__ void rot_sqrt_dev(const double* A, double* S)
 {
     double q[4];
     rot_to_quat(A, q);
-    // half-angle quaternion: (1 + q) / |1 + q|, |1 + q|^2 = 2 (1 + w)
-    const double inv = rsqrt(2.0 * (1.0 + q[0]));
-    const double a = (1.0 + q[0]) * inv, b = q[1] * inv, c = q[2] * inv, d = q[3] * inv;
+    // half-angle quaternion (1 + q) / |1 + q|, the norm taken in full so that S is a rotation to
+    // rounding whether or not |q| = 1 exactly (one reciprocal square root for both
+    // normalisations; for a unit q, |1 + q|^2 = 2 (1 + w))
+    const double w1 = 1.0 + q[0];
+    const double inv = rsqrt(w1 * w1 + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const double a = w1 * inv, b = q[1] * inv, c = q[2] * inv, d = q[3] * inv;
     S[0] = 1.0 - 2.0 * (c * c + d * d);
     S[1] = 2.0 * (b * c - a * d);
     S[2] = 2.0 * (b * d + a * c);
@@ -124,9 +123,9 @@ __device__ __forceinline__ void segment_core(const mrs_rod_params& P, const doub
     for (int i = 0; i < 3; ++i) {
         const double Fi = P.b[i] * (dot3(e, Dh + 3 * i) - (i == 2 ? 1.0 : 0.0));
         const int j = (i + 1) % 3, l = (i + 2) % 3;
-        const double dD[3] = {(Dk1[3 * j] - Dk[3 * j]) * ids, (Dk1[3 * j + 1] - Dk[3 * j + 1]) * ids,
-                              (Dk1[3 * j + 2] - Dk[3 * j + 2]) * ids};
-        const double Ni = P.a[i] * (dot3(dD, Dh + 3 * l) - (i == 1 ? om2 : 0.0));
+        const double dD[3] = {Dk1[3 * j] - Dk[3 * j], Dk1[3 * j + 1] - Dk[3 * j + 1],
+                              Dk1[3 * j + 2] - Dk[3 * j + 2]};
+        const double Ni = P.a[i] * (dot3(dD, Dh + 3 * l) * ids - (i == 1 ? om2 : 0.0));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             F[c] += Fi * Dh[3 * i + c];
