@@ -364,8 +364,9 @@ def extra_parareal(ctx, dev):
     torch.cuda.synchronize()
     t_serial1 = time.perf_counter() - t0
     # the float32 pair sum puts a floor of ~1e-8 on the relative increment for this system (a
-    # rounding flip of a packed position moves the velocities at the 1e-7 level): tol above it
-    tol1 = 1e-8
+    # rounding flip of a packed position moves the velocities at the 1e-7 level; measured
+    # increments after the third iteration stall between 0.8e-8 and 1.5e-8): tol well above it
+    tol1 = 3e-8
     small = {"workload": "one rod, 128 nodes, 64 slices x 256 fine RK2 steps (dt=1e-6), coarse 16 dt",
              "tol": tol1, "serial_fine_s": t_serial1, "runs": []}
     for gs in (0, 8):
