@@ -54,7 +54,8 @@ void rod_ws_free(RodWorkspace* ws)
     if (ws->cap) cudaStreamDestroy(ws->cap);
     if (ws->plan) plan_free(ws->plan);
     void* ptrs[] = {ws->d_node_info, ws->d_chunks, ws->d_t0, ws->d_step, ws->d_FN, ws->d_Xf, ws->d_gf, ws->d_mf,
-                    ws->d_u, ws->d_w, ws->d_g64, ws->d_m64, ws->d_u64, ws->d_w64, ws->d_Xh, ws->d_Dh};
+                    ws->d_u, ws->d_w, ws->d_g64, ws->d_m64, ws->d_u64, ws->d_w64, ws->d_Xh, ws->d_Dh,
+                    ws->d_segsc};
     for (void* q : ptrs) cudaFree(q);
     delete ws;
 }
@@ -100,7 +101,8 @@ int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int
     if ((st = dalloc(&ws->d_node_info, N)) || (st = dalloc(&ws->d_chunks, chunks.size())) ||
         (st = dalloc(&ws->d_t0, n_inst)) ||
         (st = dalloc(&ws->d_step, 1)) || (st = dalloc(&ws->d_FN, 6 * N)) ||
-        (st = dalloc(&ws->d_Xh, 3 * N)) || (st = dalloc(&ws->d_Dh, 9 * N))) {
+        (st = dalloc(&ws->d_Xh, 3 * N)) || (st = dalloc(&ws->d_Dh, 9 * N)) ||
+        (st = dalloc(&ws->d_segsc, N))) {
         rod_ws_free(ws);
         return st;
     }
@@ -164,7 +166,22 @@ RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt)
     L.n_chunks = ws->n_chunks;
     L.inv_L = 1.0 / p->L;
     set_pack_reference(L, ws->n_rods, ws->rod_off.data());
+    L.segsc = (ws->segsc_k == p->wave_k && ws->segsc_L == p->L) ? ws->d_segsc : nullptr;
     return L;
+}
+
+// (Re)builds the workspace's segment table for p's wave number and rod length when they changed.
+static int rod_ws_prepare(RodWorkspace* ws, const mrs_rod_params* p, cudaStream_t s)
+{
+    if (ws->segsc_k == p->wave_k && ws->segsc_L == p->L) return MRS_OK;
+    cudaError_t e = launch_segment_table(ws->N, ws->d_node_info, p->wave_k, p->L, ws->d_segsc, s);
+    if (e != cudaSuccess) {
+        set_error("segment table kernel failed: %s", cudaGetErrorString(e));
+        return MRS_ECUDA;
+    }
+    ws->segsc_k = p->wave_k;
+    ws->segsc_L = p->L;
+    return MRS_OK;
 }
 
 int rod_ws_set_times(RodWorkspace* ws, double t_first, double dT, cudaStream_t s)
@@ -281,6 +298,8 @@ int rod_ws_steps(RodWorkspace* ws, const mrs_rod_params* p, double* X, double* D
                  int nsteps, int scheme, cudaStream_t s)
 {
     if (nsteps <= 0 || ws->N == 0) return MRS_OK;
+    int pst = rod_ws_prepare(ws, p, s);
+    if (pst) return pst;
     // small instances: every step of every instance in one launch, the state in shared memory
     // (one CTA per instance)
     if (ws->ctx->fused_steps && ws->precision != MRS_F64 && fused_fits(ws->N1)) {
@@ -325,8 +344,9 @@ int rod_forces(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_p
     MRS_CHECK_CUDA(cudaSetDevice(ctx->device));
     RodWorkspace* ws = nullptr;
     if ((st = rod_ws_get(ctx, n_rods, rod_off, 1, MRS_F64, 0.0, 0.0, &ws))) return st;
-    const RodLaunch L = rod_launch(ws, p, 0.0);
     cudaStream_t s = (cudaStream_t)stream;
+    if ((st = rod_ws_prepare(ws, p, s))) return st;
+    const RodLaunch L = rod_launch(ws, p, 0.0);
     if ((st = rod_ws_set_times(ws, 0.0, 0.0, s))) return st;
     cudaError_t e = launch_rod_forces(L, X, D, t, g, m, nullptr, nullptr, nullptr, s);
     if (e != cudaSuccess) {

@@ -23,6 +23,9 @@ struct RodLaunch {
     int n_ref;
     int ref[8];
     double ref_w;
+    // [N] (sin, cos) of k_w s_mid for the segment k+1/2 of every node (Omega_2 by angle
+    // addition, one sincos(f t) per CTA), or NULL: sin(k_w s_mid + f t) per segment
+    const double2* segsc;
 };
 
 // The reference nodes of an instance with rods rod_off[0..n_rods]: the middle node of up to 8
@@ -49,6 +52,9 @@ cudaError_t launch_rod_update64(const RodLaunch& L, const double* X0, const doub
                                 const double* u, const double* w, double h, double* X1,
                                 double* D1, bool bump_step, cudaStream_t s);
 cudaError_t launch_rot_sqrt_batch(int n, const double* R, double* S, cudaStream_t s);
+// segsc table of RodLaunch for wave number wave_k and rod length Lrod.
+cudaError_t launch_segment_table(int N, const int2* node_info, double wave_k, double Lrod,
+                                 double2* out, cudaStream_t s);
 // Fused fine propagator (one CTA per instance, state in shared memory): nsteps steps of size
 // L.dt of every instance of the batch in one launch, then the step counter advances by nsteps.
 // Usable when the instance fits shared memory (fused_fits) -- float32 pair sum.
@@ -88,6 +94,8 @@ struct RodWorkspace {
     double* d_w64 = nullptr;
     double* d_Xh = nullptr;
     double* d_Dh = nullptr;
+    double2* d_segsc = nullptr;      // RodLaunch::segsc, valid for (segsc_k, segsc_L)
+    double segsc_k = 0.0, segsc_L = -1.0;
     mrs_plan* plan = nullptr;
     cudaStream_t cap = nullptr;   // private stream used only for graph capture
     struct Graph {

@@ -142,17 +142,38 @@ __device__ __forceinline__ void segment_core(const mrs_rod_params& P, const doub
 
 // Segment k+1/2 of the batch (index idx within a rod of M nodes) at the current step's time
 // (+ t_off).
+// sc: (sin, cos) of f t for this segment's instance when L.segsc is given (the caller's CTA
+// computed them once), else NULL.
 __device__ void segment_fn(const RodLaunch& L, const double* __restrict__ X,
                            const double* __restrict__ D, double t_off, long long k, int idx, int M,
-                           double* o)
+                           double* o, const double* sc = nullptr)
 {
-    const int inst = (int)(k / L.nodes_per_inst);
-    const double t = L.t0[inst] + (double)(*L.step) * L.dt + t_off;
-    const double ds = L.p.L / (double)(M - 1);
     const double ids = (double)(M - 1) * L.inv_L;   // one division fewer per segment
-    const double s_mid = ((double)idx + 0.5) * ds;
-    const double om2 = -L.p.wave_k * L.p.wave_k * L.p.wave_A * sin(L.p.wave_k * s_mid + L.p.wave_f * t);
+    const double amp = -L.p.wave_k * L.p.wave_k * L.p.wave_A;
+    double om2;
+    if (sc) {   // Omega_2 = amp sin(k_w s_mid + f t) by angle addition (as the fused propagator)
+        const double2 v = L.segsc[k];
+        om2 = amp * (v.x * sc[1] + v.y * sc[0]);
+    } else {
+        const int inst = (int)(k / L.nodes_per_inst);
+        const double t = L.t0[inst] + (double)(*L.step) * L.dt + t_off;
+        const double s_mid = ((double)idx + 0.5) * (L.p.L / (double)(M - 1));
+        om2 = amp * sin(L.p.wave_k * s_mid + L.p.wave_f * t);
+    }
     segment_core(L.p, X + 3 * (size_t)k, D + 9 * (size_t)k, ids, om2, o);
+}
+
+__global__ void rod_segsc_kernel(int N, const int2* __restrict__ node_info, double wave_k, double Lrod,
+                                 double2* out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int2 ni = node_info[k];
+    if (ni.y < 2) return;
+    const double ds = Lrod / (double)(ni.y - 1);
+    double sk, ck;
+    sincos(wave_k * ((double)ni.x + 0.5) * ds, &sk, &ck);   // the fused propagator's expression
+    out[k] = make_double2(sk, ck);
 }
 
 __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__ X,
@@ -255,13 +276,20 @@ __global__ void __launch_bounds__(kRodChunk) rod_forces_fused_kernel(
 {
     __shared__ double sFN[kRodChunk * 6];
     __shared__ double sref[3];
+    __shared__ double ssc[2];   // sin(f t), cos(f t) of the chunk's instance
     const long long k0 = L.chunks[blockIdx.x];
     const int2 ni0 = L.node_info[k0];
     const int M = ni0.y, t = threadIdx.x;
     const int s = ni0.x - 1 + t;   // segment index within the rod
-    const bool centred = Xf && L.n_ref > 0;   // a chunk lies in one rod, hence in one instance
-    if (centred && t == 0) pack_reference(L, X + 3 * (size_t)(k0 / L.nodes_per_inst) * L.nodes_per_inst, sref);
-    if (s >= 0 && s < M - 1) segment_fn(L, X, D, t_off, k0 - 1 + t, s, M, sFN + 6 * t);
+    const int inst = (int)(k0 / L.nodes_per_inst);   // a chunk lies in one rod, hence in one instance
+    static_assert(kRodChunk > 32, "the reference point is taken by a thread of the second warp");
+    const bool centred = Xf && L.n_ref > 0;
+    if (centred && t == 32) pack_reference(L, X + 3 * (size_t)inst * L.nodes_per_inst, sref);
+    if (L.segsc) {
+        if (t == 0) sincos(L.p.wave_f * (L.t0[inst] + (double)(*L.step) * L.dt + t_off), &ssc[0], &ssc[1]);
+        __syncthreads();
+    }
+    if (s >= 0 && s < M - 1) segment_fn(L, X, D, t_off, k0 - 1 + t, s, M, sFN + 6 * t, L.segsc ? ssc : nullptr);
     __syncthreads();
     const int n = ni0.x + t - 1;   // node index within the rod
     if (t == 0 || n >= M) return;
@@ -709,6 +737,14 @@ cudaError_t launch_rod_update64(const RodLaunch& L, const double* X0, const doub
 {
     if (L.N == 0) return cudaSuccess;
     rod_update_kernel<double><<<nblk(L.N, 128), 128, 0, s>>>(L, X0, D0, u, w, h, X1, D1, bump_step ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segment_table(int N, const int2* node_info, double wave_k, double Lrod,
+                                 double2* out, cudaStream_t s)
+{
+    if (N == 0) return cudaSuccess;
+    rod_segsc_kernel<<<nblk(N, 128), 128, 0, s>>>(N, node_info, wave_k, Lrod, out);
     return cudaGetLastError();
 }
 

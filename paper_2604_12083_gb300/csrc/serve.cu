@@ -296,6 +296,7 @@ cudaError_t admit_enqueue(mrs_server* S, SJob* j)
     L.n_chunks = 0;
     L.inv_L = 1.0 / J.params.L;
     set_pack_reference(L, J.n_rods, j->rod_off.data());
+    L.segsc = nullptr;    // two-kernel force path: sin(k_w s_mid + f t) per segment
     return cudaSuccess;
 }
 
