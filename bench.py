@@ -589,7 +589,9 @@ def run_ours(args, world, rank, local, pg):
     sym = mrs.plan_config_symmetric(plan_info["config"])
     launches_per_step = 2 if sym else 1
     kernel_name = ("mrs_f32_sym + mrs_sym_reduce (whole step)" if sym else "mrs_f32_persistent")
-    lane_ops = 41.5 if sym else 50.0
+    # FP32 lane operations per ordered pair: symmetric kernel 85.4 per unordered pair (ncu
+    # instruction counters: 83 packed + the scalar fold of each source's share), ordered 50
+    lane_ops = 42.7 if sym else 50.0
 
     # ---- device-timed region: K steps, L2 flushed before each, events around each launch ----
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -690,8 +692,7 @@ def run_ours(args, world, rank, local, pg):
                      "peak_basis": "2 x 128 FP32 lanes x %d SMs x %.0f MHz (max SM clock)" %
                                    (ctx.num_sms, mhz),
                      "flops_per_pair": FLOPS_PER_PAIR, "kernel": kernel_name,
-                     # FP32 lane operations the kernel executes per ordered pair (83 per
-                     # unordered pair for the symmetric kernel, 50 for the ordered one), and the
+                     # FP32 lane operations the kernel executes per ordered pair, and the
                      # share of the 128 lanes x SMs x clock they occupy at this rate
                      "lane_ops_per_pair": lane_ops,
                      "fp32_lane_fraction": value / world * lane_ops / (128.0 * ctx.num_sms * mhz * 1e6),
