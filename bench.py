@@ -742,6 +742,41 @@ def run_ours(args, world, rank, local, pg):
     ctx.close()
 
 
+def run_small_systems(args):
+    """Latency of one pair sum (the library's default plan, MRS_F32_COMP) on single systems of
+    1024 .. 16384 points, the sizes where a call is launch- and latency-bound; 200 back-to-back
+    calls per size, CUDA events.  Inputs stay in L2: this is the latency a time step sees."""
+    import numpy as np
+    import torch
+    from paper_2604_12083_gb300 import build as B, mrs
+    B.build()
+    ctx = mrs.Context(0)
+    out = {"case": "small_systems", "unit": "us per call", "precision": "MRS_F32_COMP",
+           "sizes": []}
+    for N in (1024, 2048, 4096, 8192, 16384):
+        rng = np.random.default_rng(N)
+        X = torch.from_numpy((rng.random((N, 3)) * 2.0).astype(np.float32)).cuda()
+        f = torch.from_numpy(rng.standard_normal((N, 3)).astype(np.float32)).cuda()
+        n = torch.from_numpy(rng.standard_normal((N, 3)).astype(np.float32)).cuda()
+        u, w = torch.empty_like(X), torch.empty_like(X)
+        pl = mrs.Plan(ctx, np.array([0, N], np.int64), 1.0, 0.01, precision=mrs.MRS_F32_COMP)
+        for _ in range(10):
+            pl.execute(X, f, n, u, w)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(200):
+            pl.execute(X, f, n, u, w)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1000.0 / 200
+        out["sizes"].append({"points": N, "us_per_call": us, "pairs_per_s": N * N / (us * 1e-6),
+                             "plan": pl.info()})
+        pl.close()
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -752,9 +787,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--config", type=int, default=-1,
                     help="force this pair-sum plan configuration (default: the library's choice)")
-    ap.add_argument("--case", choices=["main", "rod_kernels", "parareal"], default="main",
+    ap.add_argument("--case", choices=["main", "rod_kernels", "parareal", "small_systems"],
+                    default="main",
                     help="rod_kernels: time the rod force and update kernels on 1M nodes; "
-                         "parareal: the Parareal measurements alone")
+                         "parareal: the Parareal measurements alone; small_systems: latency of "
+                         "one pair sum on single systems of 1k..16k points")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -766,6 +803,9 @@ def main():
         return
     if args.case == "rod_kernels":
         run_rod_kernels(args)
+        return
+    if args.case == "small_systems":
+        run_small_systems(args)
         return
     if args.case == "parareal":
         import torch
