@@ -777,6 +777,85 @@ def run_small_systems(args):
     ctx.close()
 
 
+# GPU seconds per call that the paper prints for its own sizes (Table 1: rods of 51 points,
+# eps = 4 ds, an NVIDIA A100 PCIe with numba.cuda, a wall and Lennard-Jones terms in the model,
+# per time step or per solve not stated): MRS velocity computation, force initialisation,
+# triad update.  Context for the same calls measured here, not a target.
+PAPER_TABLE1_GPU_S = {1: (0.000389, 0.000683, 0.000230), 4: (0.000381, 0.000680, 0.000229),
+                      12: (0.000382, 0.000676, 0.000230), 25: (0.000386, 0.000687, 0.000638)}
+
+
+def run_paper_sizes(args):
+    """The paper's own problem sizes (1, 4, 12, 25 rods of 51 points, eps = 4 ds): per-call
+    latency of mrs_velocity, rod_forces and rod_advance, and of one Euler rod_step (forces,
+    pack, pair sum, update), 200 back-to-back calls each, CUDA events; beside the GPU times the
+    paper prints for the first three (Table 1, other hardware: context only)."""
+    import numpy as np
+    import torch
+    from paper_2604_12083_gb300 import build as B, mrs, workloads as W
+    B.build()
+    dev = torch.device("cuda", 0)
+    ctx = mrs.Context(0)
+    c = W.ROD_PLAIN
+    M = 51
+    eps = 4.0 / (M - 1)
+    stream = torch.cuda.current_stream(dev)
+
+    def per_call_us(fn, reps=200):
+        for _ in range(10):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1000.0 / reps
+
+    out = {"case": "paper_sizes", "unit": "us per call",
+           "workload": "n rods x 51 points, eps = 4 ds, mu = 1, free space (no wall, no LJ)",
+           "paper_context": "GPU times printed in the paper's Table 1 (A100 PCIe, numba.cuda; "
+                            "other hardware and model terms): context, not a target",
+           "rows": []}
+    for n_rods in (1, 4, 12, 25):
+        rs = W.rod_system(30 + n_rods, n_rods, M, box=3.0)
+        prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"], 1.0, eps)
+        N = rs.X.shape[0]
+        X = torch.from_numpy(rs.X).to(dev)
+        D = torch.from_numpy(rs.D).to(dev)
+        rng = np.random.default_rng(n_rods)
+        X32 = X.float()
+        f32 = torch.from_numpy(rng.standard_normal((N, 3)).astype(np.float32)).to(dev)
+        n32 = torch.from_numpy(rng.standard_normal((N, 3)).astype(np.float32)).to(dev)
+        u, w = torch.empty_like(X32), torch.empty_like(X32)
+        g, m = torch.empty_like(X), torch.empty_like(X)
+        off = np.array([0, N], np.int64)
+        t_v = per_call_us(lambda: mrs.mrs_velocity(ctx, off, X32, f32, n32, u, w, 1.0, eps))
+        t_f = per_call_us(lambda: mrs.rod_forces(ctx, rs.rod_off, prm, X, D, 0.1, g, m))
+        ua, wa = (u * 1e-3).contiguous(), (w * 1e-3).contiguous()
+        t_a = per_call_us(lambda: mrs.rod_advance(ctx, X, D, ua, wa, 1e-7))
+        Xs, Ds = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
+        mrs.rod_step(ctx, rs.rod_off, prm, Xs, Ds, 0.0, c["dt"], 16, mrs.MRS_EULER)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mrs.rod_step(ctx, rs.rod_off, prm, Xs, Ds, 0.0, c["dt"], 200, mrs.MRS_EULER)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_s = a.elapsed_time(b) * 1000.0 / 200
+        pv, pf, pa = PAPER_TABLE1_GPU_S[n_rods]
+        out["rows"].append({
+            "rods": n_rods, "points": N,
+            "mrs_velocity_us": t_v, "rod_forces_us": t_f, "rod_advance_us": t_a,
+            "rod_step_euler_us_per_step": t_s,
+            "paper_gpu_us": {"mrs_velocity": pv * 1e6, "forces": pf * 1e6, "update": pa * 1e6},
+            "paper_over_ours": {"mrs_velocity": pv * 1e6 / t_v, "forces": pf * 1e6 / t_f,
+                                "update": pa * 1e6 / t_a}})
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -787,11 +866,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--config", type=int, default=-1,
                     help="force this pair-sum plan configuration (default: the library's choice)")
-    ap.add_argument("--case", choices=["main", "rod_kernels", "parareal", "small_systems"],
+    ap.add_argument("--case", choices=["main", "rod_kernels", "parareal", "small_systems",
+                                       "paper_sizes"],
                     default="main",
                     help="rod_kernels: time the rod force and update kernels on 1M nodes; "
                          "parareal: the Parareal measurements alone; small_systems: latency of "
-                         "one pair sum on single systems of 1k..16k points")
+                         "one pair sum on single systems of 1k..16k points; paper_sizes: "
+                         "per-call latency at the paper's own sizes (1..25 rods of 51 points)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -806,6 +887,9 @@ def main():
         return
     if args.case == "small_systems":
         run_small_systems(args)
+        return
+    if args.case == "paper_sizes":
+        run_paper_sizes(args)
         return
     if args.case == "parareal":
         import torch

@@ -85,14 +85,16 @@ MRS_API int mrs_ctx_destroy(mrs_ctx* ctx);
 /* Number of SMs of the context's device (host-side query; no GPU work). */
 MRS_API int mrs_ctx_num_sms(const mrs_ctx* ctx);
 
-/* Rod stepping path of the context (rod_step, parareal_run, parareal_run_pipelined).  With
- * enable = 1 (the default) a batch of small instances -- at most ~600 nodes each (the state
- * must fit shared memory), float32 pair sum -- advances through all its steps in ONE launch:
- * one CTA per instance keeps the instance's state in shared memory and runs forces (with the
- * Lennard-Jones repulsion when enabled), pair sum and update of every stage back to back.  With
- * enable = 0, or for larger instances or MRS_F64, every step is forces -> pair-sum plan ->
- * update kernels replayed from captured CUDA graphs.  Both compute the same steps; results agree to float32 rounding of the
- * pair sum.  Host only.  Errors: MRS_EINVAL. */
+/* Rod stepping path of the context (rod_step, parareal_run, parareal_run_pipelined).  The fused
+ * path advances a batch of instances through all its steps in ONE launch: one CTA per instance
+ * keeps the instance's state in shared memory and runs forces (with the Lennard-Jones repulsion
+ * when enabled), float32 pair sum and update of every stage back to back.  The other path runs
+ * every step as forces -> pair-sum plan -> update kernels replayed from captured CUDA graphs,
+ * over all SMs.  mode = 1 (the default): fused for instances of at most 128 nodes, where one SM
+ * per instance is the faster choice; mode = 2: fused whenever the instance fits shared memory
+ * (at most ~600 nodes); mode = 0: never.  MRS_F64 stepping always takes the graphs.  Both paths
+ * compute the same steps; results agree to float32 rounding of the pair sum.  Host only.
+ * Errors: MRS_EINVAL (mode outside 0..2). */
 MRS_API int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable);
 
 /* Device-side anomaly flags raised by the pair-sum kernels of this context since the last call

@@ -456,8 +456,8 @@ int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable)
 {
     clear_error();
     MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
-    MRS_REQUIRE(enable == 0 || enable == 1, "enable must be 0 or 1");
-    ctx->fused_steps = enable != 0;
+    MRS_REQUIRE(enable >= 0 && enable <= 2, "mode must be 0, 1 or 2 (got %d)", enable);
+    ctx->fused_steps = enable;
     return MRS_OK;
 }
 

@@ -271,8 +271,9 @@ struct mrs_ctx {
     size_t rod_ws_max = 256;
     // measured best kernel configurations (mrs_autotune)
     std::vector<mrs::TuneEntry> tuned;
-    // rod stepping of small systems in one fused launch per call (mrs_ctx_set_fused_steps)
-    bool fused_steps = true;
+    // rod stepping in one fused launch per call (mrs_ctx_set_fused_steps): 0 never, 1 for
+    // instances of at most kFusedAutoNodes nodes, 2 whenever the instance fits shared memory
+    int fused_steps = 1;
 };
 
 namespace mrs {

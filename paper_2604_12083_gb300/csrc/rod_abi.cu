@@ -302,7 +302,9 @@ int rod_ws_steps(RodWorkspace* ws, const mrs_rod_params* p, double* X, double* D
     if (pst) return pst;
     // small instances: every step of every instance in one launch, the state in shared memory
     // (one CTA per instance)
-    if (ws->ctx->fused_steps && ws->precision != MRS_F64 && fused_fits(ws->N1)) {
+    const int fmode = ws->ctx->fused_steps;
+    if (fmode > 0 && ws->precision != MRS_F64 && fused_fits(ws->N1) &&
+        (fmode == 2 || ws->N1 <= kFusedAutoNodes)) {
         const RodLaunch L = rod_launch(ws, p, dt);
         cudaError_t e = launch_rod_fine_fused(L, X, D, nsteps, scheme, p->mu, p->eps, s);
         if (e != cudaSuccess) {

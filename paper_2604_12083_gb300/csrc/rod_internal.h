@@ -59,6 +59,11 @@ cudaError_t launch_segment_table(int N, const int2* node_info, double wave_k, do
 // L.dt of every instance of the batch in one launch, then the step counter advances by nsteps.
 // Usable when the instance fits shared memory (fused_fits) -- float32 pair sum.
 constexpr size_t kFusedMaxSmem = 200 * 1024;
+// Largest instance the fused path takes by default.  Measured on GB300 (us per Euler step of a
+// single instance, fused / graphs): 51 nodes 16.2 / 21.4, 128 nodes 22.6 / 22.7, 192 nodes
+// 39.0 / 22.6, 512 nodes 163 / 26.5; 64-slice Parareal batches tie at 128 nodes and favour the
+// graphs from 192 on (3.6x at 512): one SM per instance stops paying beyond ~128 nodes.
+constexpr int kFusedAutoNodes = 128;
 size_t fused_smem_bytes(int N1);
 bool fused_fits(int N1);
 cudaError_t launch_rod_fine_fused(const RodLaunch& L, double* X, double* D, int nsteps, int scheme,

@@ -195,10 +195,10 @@ class Context:
     def num_sms(self) -> int:
         return int(lib().mrs_ctx_num_sms(self.handle))
 
-    def set_fused_steps(self, enable: bool) -> None:
-        """``mrs_ctx_set_fused_steps``: one fused launch per rod-stepping call for small
-        instances (default) or the per-step kernel graphs."""
-        _check(lib().mrs_ctx_set_fused_steps(self.handle, 1 if enable else 0))
+    def set_fused_steps(self, mode: int) -> None:
+        """``mrs_ctx_set_fused_steps``: 1 (default) one fused launch per rod-stepping call for
+        instances of at most 128 nodes, 2 whenever the instance fits shared memory, 0 never."""
+        _check(lib().mrs_ctx_set_fused_steps(self.handle, int(mode)))
 
     def device_status(self) -> int:
         """``mrs_device_status``: anomaly flags since the last call (synchronizes, clears)."""

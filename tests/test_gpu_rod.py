@@ -179,6 +179,8 @@ def test_rod_invalid_arguments(ctx):
     with pytest.raises(mrs.MrsError):
         mrs.rod_step(ctx, [0, 1, 4], gp, X, D, 0.0, 1e-6, 1, 0)      # 1-node rod
     with pytest.raises(mrs.MrsError):
+        ctx.set_fused_steps(3)                                        # modes are 0, 1, 2
+    with pytest.raises(mrs.MrsError):
         mrs.rod_step(ctx, [0, 4], gp, X, D, 0.0, -1.0, 1, 0)          # dt < 0
     with pytest.raises(mrs.MrsError):
         mrs.parareal_run(ctx, [0, 4], gp, X, D, 0.0, 1e-3, 3, 1e-4, 4, 3, 1e-9)  # ragged slices
@@ -323,7 +325,7 @@ def test_fused_and_graph_stepping_agree(ctx, orc, scheme):
         gp, op = params(cfg, rs.eps)
         out = []
         try:
-            for mode in (1, 0):       # fused (one launch per call), per-step graphs
+            for mode in (2, 0):       # fused (one launch per call), per-step graphs
                 ctx.set_fused_steps(mode)
                 Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
                 mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, t0, dt, 200, scheme)
@@ -350,7 +352,7 @@ def test_parareal_fused_and_graph_fine_solves_agree(ctx):
     T1 = Ns * 16 * dt
     res = []
     try:
-        for mode in (1, 0):
+        for mode in (2, 0):
             ctx.set_fused_steps(mode)
             Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
             st = mrs.parareal_run(ctx, rs.rod_off, gp, Xd, Dd, 0.0, T1, Ns, dt, r, Ns, 1e-10)
@@ -379,7 +381,7 @@ def test_fused_and_graph_stepping_agree_with_lj(ctx):
         for lj in (0.0, 0.05):
             gp = mrs.RodParams.make(cfg["L"], cfg["a"], cfg["b"], cfg["wave_A"], cfg["wave_k"],
                                     cfg["wave_f"], 1.0, eps, lj_eps=lj)
-            for fused in (1, 0):
+            for fused in (2, 0):
                 ctx.set_fused_steps(fused)
                 Xd, Dd = torch.from_numpy(X.copy()).cuda(), torch.from_numpy(D.copy()).cuda()
                 mrs.rod_step(ctx, off, gp, Xd, Dd, 0.0, 2e-6, 60, mrs.MRS_RK2)
@@ -387,9 +389,9 @@ def test_fused_and_graph_stepping_agree_with_lj(ctx):
                 out[(lj, fused)] = Xd.cpu().numpy()
     finally:
         ctx.set_fused_steps(1)
-    assert np.isfinite(out[(0.05, 1)]).all()
-    assert rel(out[(0.05, 1)] - X, out[(0.05, 0)] - X) < 1e-5
-    assert rel(out[(0.0, 1)] - X, out[(0.0, 0)] - X) < 1e-5
+    assert np.isfinite(out[(0.05, 2)]).all()
+    assert rel(out[(0.05, 2)] - X, out[(0.05, 0)] - X) < 1e-5
+    assert rel(out[(0.0, 2)] - X, out[(0.0, 0)] - X) < 1e-5
     assert rel(out[(0.05, 0)] - X, out[(0.0, 0)] - X) > 1e-3      # the repulsion acts
 
 
@@ -448,8 +450,8 @@ def test_parareal_full_size_workload(ctx, orc, group_size):
 def test_ragged_rod_batch(ctx, orc):
     """Unit rods of 2, 3, 5, 127, 128, 129, 255 and 300 nodes in one call (node spacings from 1
     to 1/299, around the fused force kernel's chunks of 127 nodes): rod_forces against the
-    oracle, and 30 RK2 steps on both stepping paths (fused launch, kernel graphs) against the
-    oracle's."""
+    oracle, and 30 RK2 steps against the oracle's (949 nodes exceed the fused propagator's
+    shared memory, so even mode 2 takes the kernel graphs)."""
     from paper_2604_12083_gb300 import mrs, workloads as W
     sizes = [2, 3, 5, 127, 128, 129, 255, 300]
     rng = np.random.default_rng(86)
@@ -475,7 +477,7 @@ def test_ragged_rod_batch(ctx, orc):
     dt = 2e-7                               # resolves the stiffest mode of the 300-node rod
     Xo, _ = orc.rod_step(off, X, D, op, eps, 1.0, 0.0, dt, 30, mrs.MRS_RK2)
     try:
-        for fused in (1, 0):
+        for fused in (2, 0):
             ctx.set_fused_steps(fused)
             Xs_, Ds_ = torch.from_numpy(X.copy()).cuda(), torch.from_numpy(D.copy()).cuda()
             mrs.rod_step(ctx, off, gp, Xs_, Ds_, 0.0, dt, 30, mrs.MRS_RK2)
@@ -499,7 +501,7 @@ def test_rod_far_from_the_origin(ctx, orc):
     Xo, _ = orc.rod_step(rs.rod_off, rs.X + shift, rs.D, op, rs.eps, 1.0, 0.0, dt, 200, mrs.MRS_RK2)
     disp_o = Xo - (rs.X + shift)
     try:
-        for fused in (1, 0):
+        for fused in (2, 0):
             ctx.set_fused_steps(fused)
             out = []
             for sh in (shift, np.zeros(3)):
