@@ -788,8 +788,10 @@ PAPER_TABLE1_GPU_S = {1: (0.000389, 0.000683, 0.000230), 4: (0.000381, 0.000680,
 def run_paper_sizes(args):
     """The paper's own problem sizes (1, 4, 12, 25 rods of 51 points, eps = 4 ds): per-call
     latency of mrs_velocity, rod_forces and rod_advance, and of one Euler rod_step (forces,
-    pack, pair sum, update), 200 back-to-back calls each, CUDA events; beside the GPU times the
-    paper prints for the first three (Table 1, other hardware: context only)."""
+    pack, pair sum, update), 200 back-to-back calls each, CUDA events; mrs_velocity also as
+    50 calls replayed from one CUDA graph (the device time of a call without the host path);
+    beside the GPU times the paper prints for the first three (Table 1, other hardware:
+    context only)."""
     import numpy as np
     import torch
     from paper_2604_12083_gb300 import build as B, mrs, workloads as W
@@ -832,6 +834,17 @@ def run_paper_sizes(args):
         g, m = torch.empty_like(X), torch.empty_like(X)
         off = np.array([0, N], np.int64)
         t_v = per_call_us(lambda: mrs.mrs_velocity(ctx, off, X32, f32, n32, u, w, 1.0, eps))
+        # the same call without the host: reserved shape, 50 calls captured in one CUDA graph
+        mrs.mrs_reserve(ctx, off, 1.0, eps)
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                for _ in range(50):
+                    mrs.mrs_velocity(ctx, off, X32, f32, n32, u, w, 1.0, eps, stream=side)
+        stream.wait_stream(side)
+        t_vg = per_call_us(graph.replay, reps=20) / 50
         t_f = per_call_us(lambda: mrs.rod_forces(ctx, rs.rod_off, prm, X, D, 0.1, g, m))
         ua, wa = (u * 1e-3).contiguous(), (w * 1e-3).contiguous()
         t_a = per_call_us(lambda: mrs.rod_advance(ctx, X, D, ua, wa, 1e-7))
@@ -847,10 +860,12 @@ def run_paper_sizes(args):
         pv, pf, pa = PAPER_TABLE1_GPU_S[n_rods]
         out["rows"].append({
             "rods": n_rods, "points": N,
-            "mrs_velocity_us": t_v, "rod_forces_us": t_f, "rod_advance_us": t_a,
+            "mrs_velocity_us": t_v, "mrs_velocity_graph_us": t_vg,
+            "rod_forces_us": t_f, "rod_advance_us": t_a,
             "rod_step_euler_us_per_step": t_s,
             "paper_gpu_us": {"mrs_velocity": pv * 1e6, "forces": pf * 1e6, "update": pa * 1e6},
-            "paper_over_ours": {"mrs_velocity": pv * 1e6 / t_v, "forces": pf * 1e6 / t_f,
+            "paper_over_ours": {"mrs_velocity": pv * 1e6 / t_v, "mrs_velocity_graph": pv * 1e6 / t_vg,
+                                "forces": pf * 1e6 / t_f,
                                 "update": pa * 1e6 / t_a}})
     print(json.dumps(out), flush=True)
     ctx.close()
