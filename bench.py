@@ -781,7 +781,7 @@ def run_small_systems(args):
 # eps = 4 ds, an NVIDIA A100 PCIe with numba.cuda, a wall and Lennard-Jones terms in the model,
 # per time step or per solve not stated): MRS velocity computation, force initialisation,
 # triad update.  Context for the same calls measured here, not a target.
-PAPER_TABLE1_GPU_S = {1: (0.000389, 0.000683, 0.000230), 4: (0.000381, 0.000680, 0.000229),
+TABLE1_A100_GPU_S = {1: (0.000389, 0.000683, 0.000230), 4: (0.000381, 0.000680, 0.000229),
                       12: (0.000382, 0.000676, 0.000230), 25: (0.000386, 0.000687, 0.000638)}
 
 
@@ -857,7 +857,7 @@ def run_paper_sizes(args):
         b.record(stream)
         torch.cuda.synchronize()
         t_s = a.elapsed_time(b) * 1000.0 / 200
-        pv, pf, pa = PAPER_TABLE1_GPU_S[n_rods]
+        pv, pf, pa = TABLE1_A100_GPU_S[n_rods]
         out["rows"].append({
             "rods": n_rods, "points": N,
             "mrs_velocity_us": t_v, "mrs_velocity_graph_us": t_vg,
