@@ -421,7 +421,7 @@ def extra_serve(ctx, dev):
     same jobs run one request per launch, both on this GPU."""
     import torch
     from paper_2604_12083_gb300 import mrs, workloads as W
-    c = W.ROD_PLAIN
+    c = W.ROD_SERVE
     out = {"workload": "Poisson arrivals, 70% mrs_velocity / 30% 100-step Euler rod jobs, "
                        "N log-uniform [1k,64k], HBM budget 150 GB"}
     for label, rate, window, seed in (("nominal_2000_per_s", 2000.0, 0.05, 5),

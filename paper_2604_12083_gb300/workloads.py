@@ -214,5 +214,9 @@ def serve_trace(seed: int = 5, rate_hz: float = 2000.0, window_s: float = 2.0,
 WAVE = dict(L=1.0, wave_A=0.05, wave_k=2.0 * math.pi, wave_f=2.0 * math.pi)
 ROD_PLAIN = dict(WAVE, a=(0.02, 0.02, 0.02), b=(140.0, 140.0, 140.0), dt=1e-6)
 ROD_PARAREAL = dict(WAVE, a=(1.5e-5, 1.5e-5, 1.5e-5), b=(1.8, 1.8, 1.8), dt=1e-6)
+# serving rod jobs: filaments of 256 nodes, explicit Euler at dt = 1e-6; bending stiffens as
+# M^4 and stretching as M^2 (lambda_max ~ 3.1e8 a and 2.3e3 b at 256 nodes), so a = 1e-3,
+# b = 20 give lambda_max dt ~ 0.3 (ROD_PLAIN's moduli would give ~6: unstable)
+ROD_SERVE = dict(WAVE, a=(1e-3, 1e-3, 1e-3), b=(20.0, 20.0, 20.0), dt=1e-6)
 #   Parareal on one 128-node rod, fine dt = 1e-6, coarse 16 dt: lambda_max * 16 dt ~ 1.2
 ROD_PARAREAL_128 = dict(WAVE, a=(4e-3, 4e-3, 4e-3), b=(28.0, 28.0, 28.0), dt=1e-6)

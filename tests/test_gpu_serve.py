@@ -224,3 +224,66 @@ def test_served_rod_job_with_lennard_jones(ctx):
         assert rel(out[(lj, "serve")] - X, ref) < 1e-5
         assert rel(out[(lj, 2)] - X, ref) < 1e-5
     assert rel(out[(0.05, "serve")] - X, out[(0.0, "serve")] - X) > 1e-3
+
+
+def test_full_size_serving_mix(ctx):
+    """The serving workload at full size: the first 10 ms of the nominal Poisson trace (2000
+    jobs/s, 70 % single pair sums, 30 % 100-step Euler rod integrations, N log-uniform in
+    [1k, 64k], filaments of 256 nodes in a 10^3 box), all submitted before the server drains
+    them together.  Velocity jobs match the oracle on 128 sampled targets each; rod jobs equal
+    rod_step run alone, and the smallest one matches the oracle's 100 steps."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    import oracle
+    oracle.build()
+    c = W.ROD_SERVE
+    trace = W.serve_trace(seed=5, rate_hz=2000.0, window_s=0.01)
+    assert len(trace) >= 10 and max(N for _, _, N in trace) > 16384
+    rng = np.random.default_rng(5)
+    jobs = []
+    for (_, kind, N) in trace:
+        X, D = W.place_filaments(rng, N // 256, 256, box=10.0)
+        eps = float(np.float32(W.EPS_OVER_DS / 255))
+        if kind == 0:
+            f = rng.standard_normal((N, 3)).astype(np.float32)
+            n = rng.standard_normal((N, 3)).astype(np.float32)
+            jobs.append((kind, N, eps, (X.astype(np.float32), f, n)))
+        else:
+            jobs.append((kind, N, eps, (X, D, np.arange(0, N + 1, 256, dtype=np.int64))))
+    srv = mrs.Server(ctx, 32 << 30, 256)
+    bufs = []
+    try:
+        for kind, N, eps, h in jobs:
+            if kind == 0:
+                b = [torch.from_numpy(a).cuda() for a in h]
+                b += [torch.full_like(b[0], float("nan")), torch.full_like(b[0], float("nan"))]
+                t = srv.submit_velocity(b[0], b[1], b[2], b[3], b[4], 1.0, eps)
+            else:
+                b = [torch.from_numpy(h[0].copy()).cuda(), torch.from_numpy(h[1].copy()).cuda()]
+                prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"],
+                                         c["wave_f"], 1.0, eps)
+                t = srv.submit_rod(h[2], b[0], b[1], prm, 0.0, c["dt"], 100, mrs.MRS_EULER, 1.0, eps)
+            bufs.append((t, b))
+        srv.drain(600.0)
+        assert srv.stats()["symmetric_iterations"] >= 1
+        assert all(srv.poll(t)[0] for t, _ in bufs)
+    finally:
+        srv.close()
+    smallest_rod = min((j for j in range(len(jobs)) if jobs[j][0] == 1), key=lambda j: jobs[j][1])
+    for j, ((kind, N, eps, h), (_, b)) in enumerate(zip(jobs, bufs)):
+        if kind == 0:
+            idx = np.random.default_rng(j).choice(N, 128, replace=False)
+            ur, wr = oracle.mrs_velocity(h[0], h[1], h[2], eps, 1.0, xt=h[0][idx])
+            assert rel(b[3].cpu().numpy()[idx], ur) < TOL32 and rel(b[4].cpu().numpy()[idx], wr) < TOL32, (j, N)
+        else:
+            prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"],
+                                     1.0, eps)
+            Xa, Da = torch.from_numpy(h[0].copy()).cuda(), torch.from_numpy(h[1].copy()).cuda()
+            mrs.rod_step(ctx, h[2], prm, Xa, Da, 0.0, c["dt"], 100, mrs.MRS_EULER)
+            torch.cuda.synchronize()
+            disp = b[0].cpu().numpy() - h[0]
+            assert np.isfinite(disp).all()
+            assert rel(disp, Xa.cpu().numpy() - h[0]) < 1e-5, (j, N)
+            if j == smallest_rod:
+                op = oracle.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"])
+                Xo, _ = oracle.rod_step(h[2], h[0], h[1], op, eps, 1.0, 0.0, c["dt"], 100, oracle.EULER)
+                assert rel(disp, Xo - h[0]) < 1e-4, (j, N)
