@@ -258,6 +258,28 @@ def test_invalid_arguments_rejected(ctx):
         mrs.mrs_velocity(ctx, [0, 4], X, X, X, u, u, 1.0, 0.1)   # overlapping outputs
     with pytest.raises(mrs.MrsError):
         mrs.mrs_velocity(ctx, [0, 4], X, X, X, u, w, 0.0, 0.1)   # mu = 0
+    bad = [
+        lambda: mrs.mrs_velocity(ctx, [0, 4], X, X, X, X, w, 1.0, 0.1),         # u aliases X
+        lambda: mrs.mrs_velocity(ctx, [0, 4], X, X, X, u, w, 1.0, 0.1, precision=7),
+        lambda: mrs.mrs_velocity(ctx, [0, 2, 4], X, X, X, u, w, 1.0, 0.1, eps_per_sys=[0.1, 0.0]),
+        lambda: mrs.mrs_velocity(ctx, [1, 4], X, X, X, u, w, 1.0, 0.1),         # offsets[0] != 0
+        lambda: mrs.mrs_velocity(ctx, [0, 4], X, X, X, u, w, 1.0, float("nan")),
+        lambda: mrs.mrs_velocity(ctx, [0, 4], X, X, X, u, w, float("inf"), 0.1),
+    ]
+    for call in bad:
+        with pytest.raises(mrs.MrsError) as e:
+            call()
+        assert e.value.status == mrs.MRS_EINVAL
+    # a source pointer that is not float-aligned, through the C entry point directly
+    import ctypes
+    Xb = torch.zeros((8, 3), device="cuda")
+    off = np.array([0, 4], np.int64)
+    st = mrs.lib().mrs_velocity(ctx.handle, 1, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                ctypes.c_void_p(Xb.data_ptr() + 2), ctypes.c_void_p(X.data_ptr()),
+                                ctypes.c_void_p(X.data_ptr()), None, ctypes.c_void_p(u.data_ptr()),
+                                ctypes.c_void_p(w.data_ptr()), 1.0, 0.1, None, mrs.MRS_F32_COMP,
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == mrs.MRS_EINVAL
     # empty problem: a no-op
     mrs.mrs_velocity(ctx, [0, 0], X, X, X, u, w, 1.0, 0.1)
 
