@@ -180,6 +180,24 @@ def test_rod_invalid_arguments(ctx):
         mrs.rod_step(ctx, [0, 1, 4], gp, X, D, 0.0, 1e-6, 1, 0)      # 1-node rod
     with pytest.raises(mrs.MrsError):
         ctx.set_fused_steps(3)                                        # modes are 0, 1, 2
+    cfg = dict(W.ROD_PLAIN)
+    zero_L = mrs.RodParams.make(0.0, cfg["a"], cfg["b"], cfg["wave_A"], cfg["wave_k"], cfg["wave_f"], 1.0, 0.01)
+    nan_a = mrs.RodParams.make(1.0, (float("nan"),) * 3, cfg["b"], cfg["wave_A"], cfg["wave_k"],
+                               cfg["wave_f"], 1.0, 0.01)
+    g = torch.zeros_like(X)
+    bad = [
+        lambda: mrs.rod_forces(ctx, [0, 4], zero_L, X, D, 0.0, g, g.clone()),        # L = 0
+        lambda: mrs.rod_forces(ctx, [0, 4], nan_a, X, D, 0.0, g, g.clone()),         # moduli
+        lambda: mrs.rod_step(ctx, [0, 4], gp, X, D, 0.0, 1e-6, 1, 2),                # scheme
+        lambda: mrs.rod_step(ctx, [0, 4], gp, X, D, 0.0, 1e-6, 1, 0, precision=9),
+        lambda: mrs.rod_step(ctx, [0, 4], gp, X, D, float("inf"), 1e-6, 1, 0),       # t0
+        lambda: mrs.parareal_run(ctx, [0, 4], gp, X, D, 0.0, 65e-6, 65, 1e-6, 1, 3, 1e-9),   # slices
+        lambda: mrs.parareal_run(ctx, [0, 4], gp, X, D, 0.0, 3e-5, 3, 1e-6, 3, 3, 1e-9),     # 10 % 3
+    ]
+    for call in bad:
+        with pytest.raises(mrs.MrsError) as e:
+            call()
+        assert e.value.status == mrs.MRS_EINVAL
     with pytest.raises(mrs.MrsError):
         mrs.rod_step(ctx, [0, 4], gp, X, D, 0.0, -1.0, 1, 0)          # dt < 0
     with pytest.raises(mrs.MrsError):
