@@ -24,9 +24,10 @@
  *    NULL = the legacy default stream) and the call returns without synchronizing, except
  *    where an entry point says otherwise.
  *  - The library allocates device memory only in the plan
- *    constructors, the first call of mrs_velocity for a given problem shape (which builds and
- *    caches a plan) and the rod/Parareal/serving set-up calls -- never on a repeated call of
- *    the same shape.  Warm a shape up before capturing its calls in a CUDA graph.
+ *    constructors, mrs_reserve, the first call of mrs_velocity for a given problem shape (which
+ *    builds and caches a plan) and the rod/Parareal/serving set-up calls -- never on a repeated
+ *    call of the same shape.  Reserve or warm a shape up before capturing its calls in a CUDA
+ *    graph.
  */
 #ifndef MRS_GB300_H
 #define MRS_GB300_H
@@ -178,10 +179,12 @@ MRS_API int mrs_velocity_noalloc(int64_t n_points, const float* X, const float* 
  *           and execution launches the persistent pair kernel plus a small deterministic
  *           reduction kernel; with other targets such a plan runs an ordered configuration.
  *           Their scratch holds one 6-vector per source slot of every work unit (about
- *           N^2 / (2 TM) * 24 bytes for one system of N points, TM = 512 or 256).
+ *           N^2 / (2 TM) * 24 bytes for one system of N points, TM = threads x points per
+ *           thread of the configuration: 384 for the default symmetric one, up to 1536).
  * A plan owns device tables and scratch; mrs_plan_execute allocates nothing and launches one
- * persistent kernel (or, for MRS_F64, one plain kernel).  Executions of the same plan must not
- * overlap on the GPU.  Arguments as for mrs_velocity. */
+ * persistent kernel (plus the reduction kernel for a symmetric configuration; for MRS_F64 one
+ * plain kernel).  Executions of the same plan must not overlap on the GPU.  Arguments as for
+ * mrs_velocity. */
 MRS_API int mrs_plan_create(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
                     const double* eps_per_sys, int precision, int config, mrs_plan** plan);
 MRS_API int mrs_plan_execute(mrs_plan* plan, const void* X, const void* f, const void* n,
