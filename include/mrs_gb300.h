@@ -261,8 +261,9 @@ MRS_API int rod_advance(mrs_ctx* ctx, int64_t N, double* X, double* D, const voi
  * packs hold positions relative to a reference point of the current state (the mean of the
  * middle nodes of up to 8 rods), so the pair sum's accuracy does not depend on where the
  * system sits; results do not depend on how a run is split into calls.
- * scheme MRS_EULER or MRS_RK2 (explicit midpoint on positions and frames).  The steps are
- * captured once into a CUDA graph per (rods, scheme) and replayed.  Synchronizes `stream`
+ * scheme MRS_EULER or MRS_RK2 (explicit midpoint on positions and frames).  Instances of at
+ * most 128 nodes run all their steps in one fused launch; larger ones replay the steps from CUDA
+ * graphs captured once per (rods, scheme) (mrs_ctx_set_fused_steps).  Synchronizes `stream`
  * only at set-up.  Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */
 MRS_API int rod_step(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_params* p,
              double* X, double* D, double t0, double dt, int nsteps, int scheme,
@@ -270,8 +271,9 @@ MRS_API int rod_step(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs
 
 /* Principal square root S (S^2 = R, rotation angle halved about the same axis) of n rotation
  * matrices (Section III-C-1, Eqs. rodrigues / halfangle), float64, device R[n][3][3] ->
- * S[n][3][3] (row-major).  Computed through the unit quaternion of R and the half-angle
- * quaternion (1+q)/|1+q|; at an angle of exactly pi either quarter turn is returned.
+ * S[n][3][3] (row-major).  Computed through the quaternion q of R and the half-angle
+ * quaternion (1+q)/|1+q|, normalised once by its full norm; at an angle of exactly pi either
+ * quarter turn is returned.
  * Errors: MRS_EINVAL, MRS_ECUDA. */
 MRS_API int rot_sqrt_batch(mrs_ctx* ctx, int n, const double* R, double* S, void* stream);
 
