@@ -189,6 +189,49 @@ def oracle_rate(p, seconds_target, seed=0):
     return nt, rate
 
 
+def plain_rod_times(ctx, dev):
+    """The plain-method configuration timed on both sides: one 128-node rod, one float64
+    mrs_velocity with Gaussian forces and torques, then 200 RK2 rod_step steps (dt = 1e-6):
+    the FP64 oracle on the host cores and the library on the GPU (CUDA events), with the
+    agreement of the two results."""
+    import torch
+    import oracle
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    pr = W.plain_rod()
+    rs = W.rod_system(1, 1, 128)
+    c = W.ROD_PLAIN
+    op = oracle.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"])
+    t0 = time.perf_counter()
+    ur, wr = oracle.mrs_velocity(pr.X, pr.f, pr.n, pr.eps[0], pr.mu)
+    Xo, _ = oracle.rod_step(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, 0.0, c["dt"], 200, oracle.RK2)
+    t_oracle = time.perf_counter() - t0
+    prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"], 1.0, rs.eps)
+    X64, f64, n64 = (torch.from_numpy(a.astype(np.float64)).to(dev) for a in (pr.X, pr.f, pr.n))
+    u64, w64 = torch.empty_like(X64), torch.empty_like(X64)
+    Xg, Dg = torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev)
+    mrs.rod_step(ctx, rs.rod_off, prm, Xg, Dg, 0.0, c["dt"], 4, mrs.MRS_RK2)   # set-up
+    mrs.mrs_velocity(ctx, pr.offsets, X64, f64, n64, u64, w64, pr.mu, float(pr.eps[0]),
+                     precision=mrs.MRS_F64)                                   # plan built
+    Xg.copy_(torch.from_numpy(rs.X))
+    Dg.copy_(torch.from_numpy(rs.D))
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    mrs.mrs_velocity(ctx, pr.offsets, X64, f64, n64, u64, w64, pr.mu, float(pr.eps[0]),
+                     precision=mrs.MRS_F64)
+    mrs.rod_step(ctx, rs.rod_off, prm, Xg, Dg, 0.0, c["dt"], 200, mrs.MRS_RK2)
+    b.record(stream)
+    torch.cuda.synchronize()
+    disp_o = Xo - rs.X
+    return {"workload": "one 128-node rod: one FP64 mrs_velocity + 200 RK2 rod_step steps "
+                        "(dt = 1e-6)",
+            "oracle_s": t_oracle, "gpu_s": a.elapsed_time(b) * 1e-3,
+            "rel_err_u_fp64": float(np.linalg.norm(u64.cpu().numpy() - ur) / np.linalg.norm(ur)),
+            "rel_err_displacement_200_steps": float(np.linalg.norm(Xg.cpu().numpy() - rs.X - disp_o)
+                                                    / np.linalg.norm(disp_o))}
+
+
 def run_reference(args, world, rank):
     """The oracle arm: FP64 CPU oracle on the same workload, bounded sample per step."""
     if rank != 0:
@@ -726,6 +769,7 @@ def run_ours(args, world, rank, local, pg):
             "u": float(np.linalg.norm(u_last[idx] - ur) / np.linalg.norm(ur)),
             "w": float(np.linalg.norm(w_last[idx] - wr) / np.linalg.norm(wr)),
             "targets_sampled": int(nt), "against": "the FP64 oracle of the cpu_baseline sample"}
+        line["cpu_baseline"]["plain_rod"] = plain_rod_times(ctx, dev)
     line["frac_of_fp32_peak"] = line["roofline"]["frac"]
     if rank == 0 and args.extras:
         line["extras"] = run_extras(ctx, dev)
