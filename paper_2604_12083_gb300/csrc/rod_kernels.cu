@@ -391,6 +391,50 @@ __device__ __forceinline__ void fused_kahan(float& sum, float& comp, float v)
     sum = t;
 }
 
+// Pair sum of point i over the sources [jb, je) of the instance (float32 packs in shared
+// memory), in 32-source chunks whose float32 partials are folded into Kahan pairs (sum, cmp),
+// both scaled by 8 pi mu (the kernels written with d s^2 = 1, as in mrs_kernels.cu).
+__device__ __forceinline__ void fused_pair_range(const FusedConst& K, const float* sXf,
+                                                 const float* sgf, const float* smf, int i,
+                                                 int jb, int je, float* sum, float* cmp)
+{
+    const float xi = sXf[3 * i], yi = sXf[3 * i + 1], zi = sXf[3 * i + 2];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        sum[q] = 0.f;
+        cmp[q] = 0.f;
+    }
+    for (int j0 = jb; j0 < je; j0 += 32) {
+        const int j1 = min(je, j0 + 32);
+        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int j = j0; j < j1; ++j) {
+            const float rx = xi - sXf[3 * j], ry = yi - sXf[3 * j + 1], rz = zi - sXf[3 * j + 2];
+            const float fx = sgf[3 * j], fy = sgf[3 * j + 1], fz = sgf[3 * j + 2];
+            const float nx = smf[3 * j], ny = smf[3 * j + 1], nz = smf[3 * j + 2];
+            const float d = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, K.e2)));
+            const float s1 = fused_rsqrt(d);
+            const float s2 = s1 * s1;
+            const float s3 = s1 * s2, s5 = s3 * s2;
+            const float h1 = fmaf(K.e2, s3, s1);
+            const float h3 = fmaf(K.c1, s5, s3);
+            const float h4 = s3 * fmaf(s2, fmaf(K.c2, s2, K.c3), -0.5f);
+            const float h5 = s5 * fmaf(K.c5, s2, 1.5f);
+            const float bf = s3 * fmaf(fx, rx, fmaf(fy, ry, fz * rz));
+            const float bn = h5 * fmaf(nx, rx, fmaf(ny, ry, nz * rz));
+            const float hx = h3 * rx, hy = h3 * ry, hz = h3 * rz;
+            // u += H1 f + H2 (f.r) r + H3 (n x r);  w += H3 (f x r) + H4 n + H5 (n.r) r
+            acc[0] += h1 * fx + bf * rx + (ny * hz - nz * hy);
+            acc[1] += h1 * fy + bf * ry + (nz * hx - nx * hz);
+            acc[2] += h1 * fz + bf * rz + (nx * hy - ny * hx);
+            acc[3] += h4 * nx + bn * rx + (fy * hz - fz * hy);
+            acc[4] += h4 * ny + bn * ry + (fz * hx - fx * hz);
+            acc[5] += h4 * nz + bn * rz + (fx * hy - fy * hx);
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) fused_kahan(sum[q], cmp[q], acc[q]);
+    }
+}
+
 // Velocities (u, w) of the instance's points for the state (sXs, sDs) at time t.  sseg[k] =
 // (1/ds of node k's rod, sin(k_w s_mid), cos(k_w s_mid)) for the segment k+1/2, so that
 // Omega_2 = -k_w^2 A (sin(k_w s_mid) cos(f t) + cos(k_w s_mid) sin(f t)) needs one sincos per
@@ -455,47 +499,42 @@ __device__ void fused_velocity(const RodLaunch& L, const FusedConst& K, int N1,
         }
         __syncthreads();
     }
-    for (int i = tid; i < N1; i += BLOCK) {
-        const float xi = sXf[3 * i], yi = sXf[3 * i + 1], zi = sXf[3 * i + 2];
+    if (2 * N1 <= BLOCK) {
+        // two threads per point: the first half of the CTA sums sources [0, half), the second
+        // [half, N1) (whole 32-source chunks), then the first adds the second's folded partial
+        constexpr int H = BLOCK / 2;
+        const int part = tid >= H ? 1 : 0, i = tid - part * H;
+        const int half = (N1 / 2 + 31) & ~31;
         float sum[6], cmp[6];
+        if (i < N1) {
+            fused_pair_range(K, sXf, sgf, smf, i, part ? half : 0, part ? N1 : half, sum, cmp);
+            if (part) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            sum[q] = 0.f;
-            cmp[q] = 0.f;
-        }
-        for (int j0 = 0; j0 < N1; j0 += 32) {
-            const int j1 = min(N1, j0 + 32);
-            float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int j = j0; j < j1; ++j) {
-                const float rx = xi - sXf[3 * j], ry = yi - sXf[3 * j + 1], rz = zi - sXf[3 * j + 2];
-                const float fx = sgf[3 * j], fy = sgf[3 * j + 1], fz = sgf[3 * j + 2];
-                const float nx = smf[3 * j], ny = smf[3 * j + 1], nz = smf[3 * j + 2];
-                const float d = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, K.e2)));
-                const float s1 = fused_rsqrt(d);
-                const float s2 = s1 * s1;
-                const float s3 = s1 * s2, s5 = s3 * s2;
-                const float h1 = fmaf(K.e2, s3, s1);
-                const float h3 = fmaf(K.c1, s5, s3);
-                const float h4 = s3 * fmaf(s2, fmaf(K.c2, s2, K.c3), -0.5f);
-                const float h5 = s5 * fmaf(K.c5, s2, 1.5f);
-                const float bf = s3 * fmaf(fx, rx, fmaf(fy, ry, fz * rz));
-                const float bn = h5 * fmaf(nx, rx, fmaf(ny, ry, nz * rz));
-                const float hx = h3 * rx, hy = h3 * ry, hz = h3 * rz;
-                // u += H1 f + H2 (f.r) r + H3 (n x r);  w += H3 (f x r) + H4 n + H5 (n.r) r
-                acc[0] += h1 * fx + bf * rx + (ny * hz - nz * hy);
-                acc[1] += h1 * fy + bf * ry + (nz * hx - nx * hz);
-                acc[2] += h1 * fz + bf * rz + (nx * hy - ny * hx);
-                acc[3] += h4 * nx + bn * rx + (fy * hz - fz * hy);
-                acc[4] += h4 * ny + bn * ry + (fz * hx - fx * hz);
-                acc[5] += h4 * nz + bn * rz + (fx * hy - fy * hx);
+                for (int c = 0; c < 3; ++c) {
+                    su[3 * i + c] = __fsub_rn(sum[c], cmp[c]);
+                    sw[3 * i + c] = __fsub_rn(sum[3 + c], cmp[3 + c]);
+                }
             }
-#pragma unroll
-            for (int q = 0; q < 6; ++q) fused_kahan(sum[q], cmp[q], acc[q]);
         }
+        __syncthreads();
+        if (!part && i < N1) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            su[3 * i + c] = __fsub_rn(sum[c], cmp[c]) * K.scale;
-            sw[3 * i + c] = __fsub_rn(sum[3 + c], cmp[3 + c]) * K.scale;
+            for (int c = 0; c < 3; ++c) {
+                fused_kahan(sum[c], cmp[c], su[3 * i + c]);
+                fused_kahan(sum[3 + c], cmp[3 + c], sw[3 * i + c]);
+                su[3 * i + c] = __fsub_rn(sum[c], cmp[c]) * K.scale;
+                sw[3 * i + c] = __fsub_rn(sum[3 + c], cmp[3 + c]) * K.scale;
+            }
+        }
+    } else {
+        for (int i = tid; i < N1; i += BLOCK) {
+            float sum[6], cmp[6];
+            fused_pair_range(K, sXf, sgf, smf, i, 0, N1, sum, cmp);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                su[3 * i + c] = __fsub_rn(sum[c], cmp[c]) * K.scale;
+                sw[3 * i + c] = __fsub_rn(sum[3 + c], cmp[3 + c]) * K.scale;
+            }
         }
     }
     __syncthreads();
