@@ -786,6 +786,48 @@ def run_ours(args, world, rank, local, pg):
     ctx.close()
 
 
+def run_batch_case(args):
+    """The batching workload alone: 512 systems (256..16384 points, filaments of 256 nodes), one
+    plan (the autotuned configuration, or --config), 3 warm-up launches and --steps timed ones
+    (L2 flushed before each, CUDA events): pairs/s and the fraction of the FP32 peak."""
+    import torch
+    from paper_2604_12083_gb300 import build as B, mrs, workloads as W
+    B.build()
+    dev = torch.device("cuda", 0)
+    ctx = mrs.Context(0)
+    p = W.batch_systems()
+    X, f, n = (torch.from_numpy(a).to(dev) for a in (p.X, p.f, p.n))
+    u, w = torch.empty_like(X), torch.empty_like(X)
+    cfg = args.config
+    if cfg < 0:
+        cfg, _ = mrs.autotune(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32, reps=2)
+    plan = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32, config=cfg)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        plan.execute(X, f, n, u, w)
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(max(1, args.steps)):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.execute(X, f, n, u, w)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    pairs = float(p.pairs)
+    peak, mhz = fp32_peak_tflops(ctx.num_sms, load_peaks())
+    t = float(np.mean(ms))
+    print(json.dumps({"case": "batch", "workload": "batch_512_systems (N_s log-uniform in "
+                      "[256,16384], filaments of 256 nodes), MRS_F32", "pairs": pairs,
+                      "ms": t, "pairs_per_s": pairs / (t * 1e-3),
+                      "frac_of_fp32_peak": FLOPS_PER_PAIR * pairs / (t * 1e-3) / 1e12 / peak,
+                      "plan": plan.info(), "steps": len(ms)}), flush=True)
+    plan.close()
+    ctx.close()
+
+
 def run_small_systems(args):
     """Latency of one pair sum (the library's default plan, MRS_F32_COMP) on single systems of
     1024 .. 16384 points, the sizes where a call is launch- and latency-bound; 200 back-to-back
@@ -926,12 +968,13 @@ def main():
     ap.add_argument("--config", type=int, default=-1,
                     help="force this pair-sum plan configuration (default: the library's choice)")
     ap.add_argument("--case", choices=["main", "rod_kernels", "parareal", "small_systems",
-                                       "paper_sizes"],
+                                       "paper_sizes", "batch"],
                     default="main",
                     help="rod_kernels: time the rod force and update kernels on 1M nodes; "
                          "parareal: the Parareal measurements alone; small_systems: latency of "
                          "one pair sum on single systems of 1k..16k points; paper_sizes: "
-                         "per-call latency at the paper's own sizes (1..25 rods of 51 points)")
+                         "per-call latency at the paper's own sizes (1..25 rods of 51 points); "
+                         "batch: the 512-system batch alone (--config to skip autotuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -949,6 +992,9 @@ def main():
         return
     if args.case == "paper_sizes":
         run_paper_sizes(args)
+        return
+    if args.case == "batch":
+        run_batch_case(args)
         return
     if args.case == "parareal":
         import torch
