@@ -968,13 +968,14 @@ def main():
     ap.add_argument("--config", type=int, default=-1,
                     help="force this pair-sum plan configuration (default: the library's choice)")
     ap.add_argument("--case", choices=["main", "rod_kernels", "parareal", "small_systems",
-                                       "paper_sizes", "batch"],
+                                       "paper_sizes", "batch", "serve"],
                     default="main",
                     help="rod_kernels: time the rod force and update kernels on 1M nodes; "
                          "parareal: the Parareal measurements alone; small_systems: latency of "
                          "one pair sum on single systems of 1k..16k points; paper_sizes: "
                          "per-call latency at the paper's own sizes (1..25 rods of 51 points); "
-                         "batch: the 512-system batch alone (--config to skip autotuning)")
+                         "batch: the 512-system batch alone (--config to skip autotuning); "
+                         "serve: the serving measurements alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -995,6 +996,14 @@ def main():
         return
     if args.case == "batch":
         run_batch_case(args)
+        return
+    if args.case == "serve":
+        import torch
+        from paper_2604_12083_gb300 import build as B, mrs
+        B.build()
+        ctx = mrs.Context(0)
+        print(json.dumps({"case": "serve", **extra_serve(ctx, torch.device("cuda", 0))}), flush=True)
+        ctx.close()
         return
     if args.case == "parareal":
         import torch
