@@ -501,10 +501,12 @@ __device__ void fused_velocity(const RodLaunch& L, const FusedConst& K, int N1,
     }
     if (2 * N1 <= BLOCK) {
         // two threads per point: the first half of the CTA sums sources [0, half), the second
-        // [half, N1) (whole 32-source chunks), then the first adds the second's folded partial
+        // [half, N1) (whole 32-source chunks), then the first adds the second's folded partial.
+        // For N1 < 32 the rounded split point would pass N1; it is clamped so that the first
+        // half takes every source and the second an empty range (a zero partial).
         constexpr int H = BLOCK / 2;
         const int part = tid >= H ? 1 : 0, i = tid - part * H;
-        const int half = (N1 / 2 + 31) & ~31;
+        const int half = min(N1, (N1 / 2 + 31) & ~31);
         float sum[6], cmp[6];
         if (i < N1) {
             fused_pair_range(K, sXf, sgf, smf, i, part ? half : 0, part ? N1 : half, sum, cmp);
