@@ -252,7 +252,7 @@ def test_rod_forces_with_lj_match_oracle(ctx, orc):
     torch.cuda.synchronize()
     go, mo = orc.rod_forces(off, X, D, op, 0.2)
     rid = np.repeat([0, 1], M)
-    lj = orc.lj_forces(X, rid, gp.lj_sigma, gp.lj_eps)
+    lj = orc.lj_forces(X, rid, 3.0 * eps, 0.05)     # the library's default sigma = 3 eps
     assert np.abs(lj).max() > 1e-3 * np.abs(go).max()       # the rods do touch
     ref = go + lj
     assert np.abs(g.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
@@ -357,6 +357,33 @@ def test_fused_and_graph_stepping_agree(ctx, orc, scheme):
             assert rel(Xf - rs.X, Xg - rs.X) < 1e-5
             assert rel(Df - rs.D, Dg - rs.D) < 1e-4
             assert rel(Xf - rs.X, Xo - rs.X) < 1e-4
+
+
+@pytest.mark.parametrize("n_rods,M", [(1, 2), (1, 16), (1, 31), (2, 10), (1, 33)])
+def test_fused_stepping_short_instances(ctx, orc, n_rods, M):
+    """Instances of fewer than 32 nodes (and one just above) take the fused path's split pair
+    sum, whose split point is rounded to whole 32-source chunks: the first half of the CTA must
+    then cover every source and read nothing past the instance.  Fused, graph and oracle
+    stepping agree over 50 Euler and 50 RK2 steps."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs = W.rod_system(90 + M, n_rods, M, box=2.0)
+    cfg = dict(W.ROD_PLAIN)
+    gp, op = params(cfg, rs.eps)
+    for scheme in (mrs.MRS_EULER, mrs.MRS_RK2):
+        out = []
+        try:
+            for mode in (2, 0):
+                ctx.set_fused_steps(mode)
+                Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
+                mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, 0.0, cfg["dt"], 50, scheme)
+                torch.cuda.synchronize()
+                out.append(Xd.cpu().numpy())
+        finally:
+            ctx.set_fused_steps(1)
+        Xo, _ = orc.rod_step(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, 0.0, cfg["dt"], 50, scheme)
+        assert np.isfinite(out[0]).all()
+        assert rel(out[0] - rs.X, out[1] - rs.X) < 1e-5
+        assert rel(out[0] - rs.X, Xo - rs.X) < 1e-4
 
 
 def test_parareal_fused_and_graph_fine_solves_agree(ctx):
