@@ -165,8 +165,13 @@ MRS_API int mrs_reserve(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double 
  * make that first call before any stream capture.  No call allocates or frees memory.  Every
  * call shares the one array and each call re-initialises what must start at zero, so calls
  * whose GPU work overlaps (other streams, other host threads) race and give wrong results:
- * issue them on one stream.
- * Errors: MRS_EINVAL, MRS_ECUDA. */
+ * issue them on one stream.  The array's address is remembered per device ordinal for the life
+ * of the process: do not call this entry point again on a device after cudaDeviceReset (or any
+ * other teardown of its primary context), which reloads the module at a new address.
+ * Non-finite inputs are NOT reported: unlike mrs_velocity, no flag reaches mrs_device_status
+ * (there is no context); the NaN/Inf shows up in u and w instead.
+ * Errors: MRS_EINVAL (size, mu, eps, NULL, outputs overlapping inputs or each other, pointers
+ *         not 4-byte aligned -- all checked before any launch), MRS_ECUDA. */
 MRS_API int mrs_velocity_noalloc(int64_t n_points, const float* X, const float* f, const float* n,
                                  float* u, float* w, double mu, double eps, void* stream);
 
@@ -230,7 +235,8 @@ typedef struct {
     double mu;         /* viscosity used by rod_step / parareal_run */
     double eps;        /* MRS regularisation used by rod_step / parareal_run */
     double lj_eps;     /* Lennard-Jones well depth between rods (Section IV-A); 0 = no repulsion */
-    double lj_sigma;   /* Lennard-Jones length sigma (the paper uses 3 eps); cut at 2^{1/6} sigma */
+    double lj_sigma;   /* Lennard-Jones length sigma, cut at 2^{1/6} sigma; <= 0 selects the
+                          paper's 3 eps (then eps must be > 0 when lj_eps > 0) */
 } mrs_rod_params;
 
 /* Point force g_k and torque m_k that every node applies to the fluid at time t (plus, when

@@ -98,6 +98,13 @@ int na_setup(int dev, unsigned char** addr, int* ctas)
     return MRS_OK;
 }
 
+bool na_overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const char* pa = (const char*)a;
+    const char* pb = (const char*)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
 }  // namespace
 }  // namespace mrs
 
@@ -117,6 +124,18 @@ extern "C" int mrs_velocity_noalloc(int64_t n_points, const float* X, const floa
     MRS_REQUIRE(std::isfinite(eps) && eps > 0.0, "eps must be > 0 (got %g)", eps);
     if (n_points == 0) return MRS_OK;
     MRS_REQUIRE(X && f && n && u && w, "NULL input or output pointer");
+    // persistent CTAs write u, w for finished tiles while others still read X, f, n as
+    // sources, so an output aliasing an input gives silently wrong sums; a float pointer that
+    // is not 4-byte aligned would fault the kernel: both are rejected before any launch
+    const size_t bytes = (size_t)n_points * 3 * sizeof(float);
+    const void* ins[3] = {X, f, n};
+    for (int i = 0; i < 3; ++i)
+        MRS_REQUIRE(!na_overlap(ins[i], bytes, u, bytes) && !na_overlap(ins[i], bytes, w, bytes),
+                    "outputs must not overlap the inputs");
+    MRS_REQUIRE(!na_overlap(u, bytes, w, bytes), "u and w must not overlap");
+    MRS_REQUIRE(((uintptr_t)X | (uintptr_t)f | (uintptr_t)n | (uintptr_t)u | (uintptr_t)w) %
+                        sizeof(float) == 0,
+                "pointers must be aligned to 4 bytes (float32)");
     int dev = 0;
     MRS_CHECK_CUDA(cudaGetDevice(&dev));
     MRS_REQUIRE(dev >= 0 && dev < 64, "device ordinal %d not supported", dev);
@@ -161,7 +180,9 @@ extern "C" int mrs_velocity_noalloc(int64_t n_points, const float* X, const floa
     L.w = w;
     L.partial = partial;
     L.counters = counters;
-    L.err = (unsigned int*)(base + kNaOffErr);   // a word of the array nobody reads back
+    // the kernel's non-finite-input flag goes to a word of the array that is never read back:
+    // this entry point does not report non-finite inputs (the outputs carry the NaN/Inf)
+    L.err = (unsigned int*)(base + kNaOffErr);
     cudaError_t e = launch_mrs_f32(kNaConfig, true, L, s);
     if (e != cudaSuccess) {
         set_error("pair-sum launch failed: %s", cudaGetErrorString(e));
