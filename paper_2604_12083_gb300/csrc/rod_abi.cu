@@ -44,6 +44,12 @@ static int check_params(const mrs_rod_params* p, bool need_fluid)
         MRS_REQUIRE(std::isfinite(p->mu) && p->mu > 0.0, "mu must be > 0");
         MRS_REQUIRE(std::isfinite(p->eps) && p->eps > 0.0, "eps must be > 0");
     }
+    MRS_REQUIRE(std::isfinite(p->lj_eps) && p->lj_eps >= 0.0, "lj_eps must be >= 0");
+    if (p->lj_eps > 0.0)
+        MRS_REQUIRE(std::isfinite(p->lj_sigma) &&
+                        (p->lj_sigma > 0.0 || (std::isfinite(p->eps) && p->eps > 0.0)),
+                    "Lennard-Jones repulsion needs lj_sigma > 0, or lj_sigma = 0 and eps > 0 "
+                    "(sigma = 3 eps)");
     return MRS_OK;
 }
 
@@ -161,6 +167,7 @@ RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt)
     L.step = ws->d_step;
     L.dt = dt;
     L.p = *p;
+    L.p.lj_sigma = lj_sigma_of(*p);
     L.FN = ws->d_FN;
     L.chunks = ws->d_chunks;
     L.n_chunks = ws->n_chunks;

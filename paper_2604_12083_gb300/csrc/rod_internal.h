@@ -123,6 +123,12 @@ cudaError_t launch_parareal_correct(int N1, const double* FpX, const double* FpD
                                     double* UD, double* incr, cudaStream_t s);
 void rod_ws_free(RodWorkspace* ws);
 RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt);
+
+// Lennard-Jones length used by the kernels: lj_sigma when > 0, else 3 eps (Section IV-A).
+inline double lj_sigma_of(const mrs_rod_params& p)
+{
+    return p.lj_sigma > 0.0 ? p.lj_sigma : 3.0 * p.eps;
+}
 // Enqueue `nsteps` steps of size dt on the workspace's state buffers X, D (device), with the
 // instance start times already set; replays captured graphs.
 int rod_ws_steps(RodWorkspace* ws, const mrs_rod_params* p, double* X, double* D, double dt,

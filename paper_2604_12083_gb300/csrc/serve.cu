@@ -291,6 +291,7 @@ cudaError_t admit_enqueue(mrs_server* S, SJob* j)
     L.step = step;
     L.dt = J.dt;
     L.p = J.params;
+    L.p.lj_sigma = lj_sigma_of(J.params);
     L.FN = FN;
     L.chunks = nullptr;   // two-kernel force path (no chunk table in the pool)
     L.n_chunks = 0;

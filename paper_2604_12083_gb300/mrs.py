@@ -68,7 +68,7 @@ class RodParams(ctypes.Structure):
             p.b[q] = b[q]
         p.wave_A, p.wave_k, p.wave_f, p.mu, p.eps = wave_A, wave_k, wave_f, mu, eps
         p.lj_eps = lj_eps
-        p.lj_sigma = 3.0 * eps if lj_sigma is None else lj_sigma
+        p.lj_sigma = 0.0 if lj_sigma is None else lj_sigma   # 0: the library's 3 eps
         return p
 
 
