@@ -210,38 +210,56 @@ def test_deterministic(ctx, config):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+def per_target_max(a, b):
+    """Largest per-target error norm over the field's RMS per-target norm: a bound that a
+    localized error (a wrong tile edge touching a few targets) cannot hide under."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.linalg.norm(a - b, axis=1)) / np.sqrt(np.mean(np.sum(b * b, axis=1))))
+
+
+PER_TARGET = 1e-4
+
+
 @pytest.mark.parametrize("config", [None, 17])
-def test_full_size_single_system_sampled(ctx, orc, config):
+def test_full_size_single_system_all_targets(ctx, orc, config):
     """32 filaments x 1024 nodes, the benchmark's launch (cached plan, default config; and the
-    symmetric configuration): 512 sampled targets against all 32768 sources, computed one by
-    one by the oracle."""
+    symmetric configuration): every one of the 32768 targets against all sources, by the
+    oracle.  Relative L2 per field <= 1e-5, and every target's error <= 1e-4 of the field's
+    RMS."""
     from paper_2604_12083_gb300 import mrs, workloads as W
     p = W.single_system()
     u, w = run(ctx, p, mrs.MRS_F32_COMP, config=config)
     assert np.isfinite(u).all() and np.isfinite(w).all()
-    idx = np.random.default_rng(64).choice(p.n_points, 512, replace=False)
-    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu, xt=p.X[idx])
-    assert rel_l2(u[idx], ur) < TOL32 and rel_l2(w[idx], wr) < TOL32
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+    assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
+    assert per_target_max(u, ur) < PER_TARGET and per_target_max(w, wr) < PER_TARGET
 
 
 @pytest.mark.parametrize("config", [None, 17])
 def test_full_size_batch_sampled(ctx, orc, config):
-    """512 systems of 256..16384 points in one persistent launch: 4 sampled targets per system
-    against all sources of their own system."""
+    """512 systems of 256..16384 points in one persistent launch: per system its first and
+    last target (system and tile edges) and 62 sampled ones against all sources of their own
+    system; relative L2 over the samples <= 1e-5 and every sampled target within 1e-4 of its
+    system's RMS (float32 accumulation without compensation in this configuration)."""
     from paper_2604_12083_gb300 import mrs, workloads as W
     p = W.batch_systems()
     u, w = run(ctx, p, mrs.MRS_F32, config=config)
+    assert np.isfinite(u).all() and np.isfinite(w).all()
     rng = np.random.default_rng(65)
     eu_n = eu_d = ew_n = ew_d = 0.0
+    worst = 0.0
     for s in range(len(p.offsets) - 1):
         a, b = int(p.offsets[s]), int(p.offsets[s + 1])
-        idx = rng.choice(b - a, 4, replace=False)
+        idx = np.unique(np.concatenate([[0, b - a - 1], rng.choice(b - a, 62, replace=False)]))
         ur, wr = orc.mrs_velocity(p.X[a:b], p.f[a:b], p.n[a:b], p.eps[s], p.mu, xt=p.X[a:b][idx])
         eu_n += np.sum((u[a:b][idx] - ur) ** 2)
         eu_d += np.sum(ur ** 2)
         ew_n += np.sum((w[a:b][idx] - wr) ** 2)
         ew_d += np.sum(wr ** 2)
+        worst = max(worst, per_target_max(u[a:b][idx], ur), per_target_max(w[a:b][idx], wr))
     assert np.sqrt(eu_n / eu_d) < TOL32 and np.sqrt(ew_n / ew_d) < TOL32
+    assert worst < PER_TARGET
 
 
 def test_invalid_arguments_rejected(ctx):
