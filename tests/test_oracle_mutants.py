@@ -75,11 +75,9 @@ ROD_MUTANTS = {
     "mid_frame_unrotated": [("Dh[3*i + r] = S[3*r + 0] * Dk[3*i + 0] + S[3*r + 1] * Dk[3*i + 1] + S[3*r + 2] * Dk[3*i + 2];",
                              "Dh[3*i + r] = Dk[3*i + r];")],
     "rodrigues_sign": [("ct * Di[q] + st * exD[q]", "ct * Di[q] - st * exD[q]")],
-    "rk2_half_step": [("rodrigues_velocities_placeholder", "")],
+    "rk2_stage_time": [("t + 0.5 * dt, g, m, u, w);", "t, g, m, u, w);"),
+                       ("Xh[q] = X[q] + u[q] * (0.5 * dt);", "Xh[q] = X[q] + u[q] * (1.0 * dt);")],
 }
-ROD_MUTANTS.pop("rk2_half_step")
-ROD_MUTANTS["rk2_stage_time"] = [("t + 0.5 * dt, g, m, u, w);", "t, g, m, u, w);"),
-                                 ("Xh[q] = X[q] + u[q] * (0.5 * dt);", "Xh[q] = X[q] + u[q] * (1.0 * dt);")]
 
 
 @pytest.mark.parametrize("name", sorted(ROD_MUTANTS))
