@@ -116,6 +116,26 @@ def test_ragged_batch_every_config(ctx, orc, config, precision):
         assert rel_l2(w[a:b], wr[a:b]) < TOL32, (s, b - a)
 
 
+@pytest.fixture(scope="module")
+def mid_system(orc):
+    """One system of 20 filaments x 1000 nodes (20000 points) and its oracle velocities: large
+    enough that every persistent CTA of every configuration sweeps several 32-source units and
+    several 128-source chunks of a tile row, which the ragged batch's small systems never do."""
+    from paper_2604_12083_gb300 import workloads as W
+    p = W.single_system(seed=66, n_fil=20, M=1000)
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+    return p, ur, wr
+
+
+@pytest.mark.parametrize("config", list(range(N_CONFIGS)))
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mid_system_every_config(ctx, mid_system, config, precision):
+    p, ur, wr = mid_system
+    u, w = run(ctx, p, precision, config=config)
+    assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
+    assert per_target_max(u, ur) < PER_TARGET and per_target_max(w, wr) < PER_TARGET
+
+
 def test_ragged_batch_float64(ctx, orc):
     from paper_2604_12083_gb300 import mrs
     p = ragged_batch()
