@@ -343,10 +343,14 @@ MRS_API int parareal_run_pipelined(mrs_ctx* ctx, int n_rods, const int64_t* rod_
  *
  * A server owns one CUDA stream, a device memory pool of hbm_budget_bytes and a scheduler
  * thread.  Jobs are admitted, in submission order, as soon as a slot (max_slots) and pool
- * memory for their footprint are free.  Every scheduler iteration advances ALL admitted jobs
- * by one stage -- a velocity job is one stage, a rod job one stage per Euler step (two per
- * RK2 step) -- and the pair sums of all of them run as ONE persistent kernel launch, so jobs
+ * memory for their footprint are free.  Every scheduler iteration advances admitted jobs by
+ * one stage -- a velocity job is one stage, a rod job one stage per Euler step (two per RK2
+ * step) -- and the pair sums of all of them run as ONE persistent kernel launch, so jobs
  * that arrive while others are on the GPU join the next iteration and their work overlaps.
+ * Which admitted jobs an iteration advances (serve_set_policy): every "small" job, and the
+ * oldest "big" one(s), a job being big when its total pair work (n_points^2 per stage times
+ * its stages) reaches a threshold.  Big jobs thus run one after another in admission order,
+ * as they would one request per launch, and small jobs never wait behind them.
  * Inputs are copied into the pool when the job is admitted and results are copied out when
  * it finishes; the caller's buffers must stay valid and unmodified until serve_poll reports
  * the job done.
@@ -406,6 +410,20 @@ MRS_API int serve_drain(mrs_server* srv, double timeout_s);
  * from the budget).  Any output pointer may be NULL. */
 MRS_API int serve_stats(mrs_server* srv, int64_t* iterations, int64_t* completed, double* pairs,
                         int* peak_active, size_t* peak_pool_bytes, int64_t* symmetric_iterations);
+
+/* Scheduling policy (host call; applies to jobs admitted from then on).  A job whose total pair
+ * work n_points^2 x stages is at least big_job_pairs is "big": each iteration advances all
+ * small jobs and only the max_big_jobs oldest big ones.  Default: 1.3e10 pair interactions
+ * (about 20 ms of the pair-sum kernel on a GB300) and 1 big job.  big_job_pairs <= 0 makes
+ * every job small (every admitted job advances in every iteration).
+ * Errors: MRS_EINVAL (non-finite threshold, max_big_jobs outside 1..4096). */
+MRS_API int serve_set_policy(mrs_server* srv, double big_job_pairs, int max_big_jobs);
+
+/* Fault injection for tests (no GPU involvement): the admission of the waiting job `ticket`
+ * fails as a pool allocation failure would -- the job finishes with MRS_ENOMEM without
+ * touching its buffers or the GPU, and the other jobs are unaffected.
+ * Errors: MRS_EINVAL (unknown ticket), MRS_EBUSY (the job is no longer waiting). */
+MRS_API int serve_inject_alloc_failure(mrs_server* srv, uint64_t ticket);
 
 /* Stop the scheduler (after the queued work finishes) and free the pool. */
 MRS_API int serve_destroy(mrs_server* srv);

@@ -4,17 +4,28 @@
 //   1. admits waiting jobs in submission order while a slot and pool memory for the job are
 //      free (admission by device-memory footprint); an admitted job's inputs are copied into
 //      the pool and, for rod jobs, its node table is set up by a kernel;
-//   2. for every admitted rod job, computes its rod forces for the current stage and packs
+//   2. picks the jobs the iteration advances: every "small" admitted job (total pair work --
+//      N^2 per stage times its stages -- below the server's big-job threshold) and the oldest
+//      max_big "big" ones.  Big jobs therefore run one after another in admission order, as
+//      they would one request per launch, while small jobs are batched along with them and
+//      never wait behind a big one;
+//   3. for every picked rod job, computes its rod forces for the current stage and packs
 //      positions, forces and torques (float32) into the job's range of the point pool;
-//   3. runs ONE persistent pair-sum launch over all admitted jobs (each job one system of the
+//   4. runs ONE persistent pair-sum launch over all picked jobs (each job one system of the
 //      batch, its own eps and mu) -- the work of every job in flight overlaps on the GPU.  The
 //      launch is the symmetric kernel (each unordered pair once, mrs_sym.cu) whenever the
 //      iteration's row and column partials fit the server's scratch, else the ordered one;
-//   4. velocity jobs copy their result out and finish; rod jobs apply the stage's update and
+//   5. velocity jobs copy their result out and finish; rod jobs apply the stage's update and
 //      finish after their last step (state copied back to the caller).
+// Why the split: when every admitted job advances in every iteration, a big rod job shares the
+// GPU with everything that arrives during its hundreds of stages and finishes later than it
+// would have alone (processor sharing), which raises the tail latency above that of one
+// request per launch; serving big jobs in order and only small ones alongside keeps the tail
+// at or below it while small jobs still finish in a few iterations.
 // At most two iterations are in flight: the host builds iteration i+1 while the GPU runs i, and
 // retires i (completion times from CUDA events, pool memory released) before building i+2.
 // Pool memory of a finished job is released only after the GPU has passed its last use.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -103,6 +114,8 @@ struct RodTable {      // passed by value to the set-up kernel (kernel parameter
 struct SJob {
     uint64_t ticket = 0;
     mrs_job spec;
+    double work = 0.0;               // total pair interactions of the job (all its stages)
+    bool big = false;                // work >= the server's big-job threshold (at admission)
     std::vector<int64_t> rod_off;
     double t_submit = 0.0, t_done = 0.0;
     int status = MRS_PENDING;
@@ -179,6 +192,9 @@ struct mrs_server {
     std::condition_variable cv, cv_done;
     std::deque<SJob*> waiting;
     std::vector<SJob*> active;
+    double big_pairs = 1.3e10;       // big-job threshold (pair interactions; <= 0: none big)
+    int max_big = 1;                 // big jobs advanced per iteration
+    uint64_t fail_ticket = 0;        // test hook: the admission of this ticket fails (ENOMEM)
     std::unordered_map<uint64_t, SJob*> jobs;
     uint64_t next_ticket = 1;
     int64_t submitted = 0, completed = 0, iterations = 0;
@@ -306,8 +322,22 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
 {
     cudaStream_t s = S->stream;
     cudaError_t e;
+    // the jobs this iteration advances: every small job and the oldest max_big big ones
+    std::vector<SJob*> run;
+    run.reserve(S->active.size());
+    {
+        int nbig = 0;
+        for (SJob* j : S->active) {
+            if (!j->big) {
+                run.push_back(j);
+            } else if (nbig < S->max_big) {
+                run.push_back(j);
+                ++nbig;
+            }
+        }
+    }
     // rod forces of the current stage, packed into each job's point range
-    for (SJob* j : S->active) {
+    for (SJob* j : run) {
         if (j->spec.kind != MRS_JOB_ROD) continue;
         const bool half = j->spec.scheme == MRS_RK2 && j->stage == 1;
         const size_t o = 3 * j->pt_off;
@@ -320,10 +350,10 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
     mrs_server::Stage& st = S->stage[S->stage_idx];
     S->stage_idx = (S->stage_idx + 1) % 3;
     if ((e = cudaEventSynchronize(st.used))) return e;   // the staging buffer is free again
-    const int n_sys = (int)S->active.size();
+    const int n_sys = (int)run.size();
     double pairs = 0.0;
     for (int q = 0; q < n_sys; ++q) {
-        SJob* j = S->active[q];
+        SJob* j = run[q];
         const double e2 = j->spec.eps * j->spec.eps;
         SysConst& c = st.sc[q];
         c.e2 = (float)e2;
@@ -338,7 +368,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
     int snt = 0;
     long long sW = 0;
     for (int q = 0; q < n_sys; ++q) {
-        SJob* j = S->active[q];
+        SJob* j = run[q];
         const long long N = j->spec.n_points;
         const int tfirst = snt;
         for (long long t = 0, k = 0; t < N; t += S->sTM, ++k) {
@@ -371,7 +401,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
     long long W = 0, max_nu = 0;
     if (!sym) {
         for (int q = 0; q < n_sys; ++q) {
-            SJob* j = S->active[q];
+            SJob* j = run[q];
             const long long N = j->spec.n_points;
             const int nu = (int)((N + kUnitSources - 1) / kUnitSources);
             for (long long t = 0; t < N; t += S->TM) {
@@ -429,8 +459,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
         if ((e = launch_mrs_f32(S->config, true, L, s))) return e;
     }
     // stage updates and copy-out
-    std::vector<SJob*> keep;
-    for (SJob* j : S->active) {
+    for (SJob* j : run) {
         const size_t N = (size_t)j->spec.n_points, o = 3 * j->pt_off;
         bool done = false;
         if (j->spec.kind == MRS_JOB_VELOCITY) {
@@ -454,9 +483,15 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
                 done = true;
             }
         }
-        if (done) finishing.push_back(j); else keep.push_back(j);
+        if (done) finishing.push_back(j);
     }
-    S->active.swap(keep);
+    if (!finishing.empty()) {
+        std::vector<SJob*> keep;
+        keep.reserve(S->active.size());
+        for (SJob* j : S->active)
+            if (std::find(finishing.begin(), finishing.end(), j) == finishing.end()) keep.push_back(j);
+        S->active.swap(keep);
+    }
     std::lock_guard<std::mutex> g(S->mu);
     S->iterations += 1;
     S->sym_iterations += sym ? 1 : 0;
@@ -501,8 +536,20 @@ void scheduler(mrs_server* S)
             // admission: submission order, while a slot and the job's footprint are free
             while (!S->waiting.empty() && (int)S->active.size() < S->max_slots) {
                 SJob* j = S->waiting.front();
+                if (j->ticket == S->fail_ticket) {
+                    // injected allocation failure: the job ends with MRS_ENOMEM, untouched
+                    S->fail_ticket = 0;
+                    S->waiting.pop_front();
+                    j->finished = true;
+                    j->status = MRS_ENOMEM;
+                    j->t_done = now_s();
+                    S->completed += 1;
+                    S->cv_done.notify_all();
+                    continue;
+                }
                 if (!reserve(S, j)) break;
                 S->waiting.pop_front();
+                j->big = S->big_pairs > 0.0 && j->work >= S->big_pairs;
                 S->active.push_back(j);
                 admitted.push_back(j);
             }
@@ -701,6 +748,8 @@ int serve_submit(mrs_server* S, const mrs_job* job, uint64_t* ticket)
         set_error("server stopped after an error");
         return S->fatal;
     }
+    j->work = (double)N * (double)N *
+              (J.kind == MRS_JOB_ROD ? (double)J.nsteps * (J.scheme == MRS_RK2 ? 2.0 : 1.0) : 1.0);
     j->ticket = S->next_ticket++;
     j->t_submit = now_s();
     S->jobs[j->ticket] = j;
@@ -723,6 +772,8 @@ int serve_poll(mrs_server* S, uint64_t ticket, int* done, double* latency_s)
     if (!j->finished) return MRS_PENDING;
     if (latency_s) *latency_s = j->t_done - j->t_submit;
     if (j->status == MRS_ECANCELED) set_error("job %llu was cancelled", (unsigned long long)ticket);
+    else if (j->status == MRS_ENOMEM && !S->fatal)
+        set_error("job %llu: pool allocation failed at admission", (unsigned long long)ticket);
     else if (j->status != MRS_OK) set_error("%s", S->fatal_msg);
     return j->status;
 }
@@ -782,6 +833,35 @@ int serve_stats(mrs_server* S, int64_t* iterations, int64_t* completed, double* 
     if (peak_active) *peak_active = S->peak_active;
     if (peak_pool_bytes) *peak_pool_bytes = S->pts.peak() * 60 + S->bytes.peak() * kByteAlign;
     if (symmetric_iterations) *symmetric_iterations = S->sym_iterations;
+    return MRS_OK;
+}
+
+int serve_set_policy(mrs_server* S, double big_job_pairs, int max_big_jobs)
+{
+    clear_error();
+    MRS_REQUIRE(S != nullptr, "NULL server");
+    MRS_REQUIRE(std::isfinite(big_job_pairs), "big_job_pairs must be finite");
+    MRS_REQUIRE(max_big_jobs >= 1 && max_big_jobs <= 4096, "max_big_jobs must be in 1..4096");
+    std::lock_guard<std::mutex> g(S->mu);
+    S->big_pairs = big_job_pairs;
+    S->max_big = max_big_jobs;
+    return MRS_OK;
+}
+
+int serve_inject_alloc_failure(mrs_server* S, uint64_t ticket)
+{
+    clear_error();
+    MRS_REQUIRE(S != nullptr, "NULL server");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->jobs.find(ticket);
+    MRS_REQUIRE(it != S->jobs.end(), "unknown ticket %llu", (unsigned long long)ticket);
+    bool waiting = false;
+    for (SJob* w : S->waiting) waiting = waiting || w == it->second;
+    if (!waiting) {
+        set_error("job %llu is not waiting for admission", (unsigned long long)ticket);
+        return MRS_EBUSY;
+    }
+    S->fail_ticket = ticket;
     return MRS_OK;
 }
 

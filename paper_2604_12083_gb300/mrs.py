@@ -32,6 +32,7 @@ EXPORTS = [
     "mrs_plan_config_count", "mrs_plan_config_symmetric", "mrs_plan_config_info", "mrs_plan_info",
     "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run", "mrs_velocity_noalloc",
     "serve_create", "serve_submit", "serve_poll", "serve_drain", "serve_stats", "serve_destroy",
+    "serve_set_policy", "serve_inject_alloc_failure",
     "serve_cancel",
     "mrs_autotune", "mrs_autotune_save", "mrs_autotune_load", "parareal_run_pipelined",
     "rod_advance", "rod_checkpoint_save", "rod_checkpoint_load", "mrs_device_status",
@@ -145,6 +146,8 @@ def lib():
         L.serve_submit.argtypes = [_vp, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]
         L.serve_poll.argtypes = [_vp, ctypes.c_uint64, _ip, _dp]
         L.serve_drain.argtypes = [_vp, ctypes.c_double]
+        L.serve_set_policy.argtypes = [_vp, ctypes.c_double, ctypes.c_int]
+        L.serve_inject_alloc_failure.argtypes = [_vp, ctypes.c_uint64]
         L.serve_cancel.argtypes = [_vp, ctypes.c_uint64]
         L.serve_stats.argtypes = [_vp, _i64p, _i64p, _dp, _ip, ctypes.POINTER(ctypes.c_size_t), _i64p]
         L.serve_destroy.argtypes = [_vp]
@@ -436,6 +439,14 @@ class Server:
         _check(st)
         self._keep.pop(ticket, None)
         return True, lat.value
+
+    def set_policy(self, big_job_pairs=1.3e10, max_big_jobs=1):
+        """``serve_set_policy``: big-job threshold (pair interactions) and big jobs per iteration."""
+        _check(lib().serve_set_policy(self.handle, float(big_job_pairs), int(max_big_jobs)))
+
+    def inject_alloc_failure(self, ticket):
+        """``serve_inject_alloc_failure``: make the admission of a waiting job fail (tests)."""
+        _check(lib().serve_inject_alloc_failure(self.handle, ctypes.c_uint64(ticket)))
 
     def cancel(self, ticket):
         """``serve_cancel``: cancel a job that has not been admitted yet."""

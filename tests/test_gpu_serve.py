@@ -287,3 +287,84 @@ def test_full_size_serving_mix(ctx):
                 op = oracle.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"])
                 Xo, _ = oracle.rod_step(h[2], h[0], h[1], op, eps, 1.0, 0.0, c["dt"], 100, oracle.EULER)
                 assert rel(disp, Xo - h[0]) < 1e-4, (j, N)
+
+
+def test_big_jobs_in_order_small_jobs_alongside(ctx):
+    """serve_set_policy: with a threshold that makes two long rod jobs "big", the second one
+    advances only after the first has finished (admission order, as one request per launch
+    would run them), velocity jobs submitted after both still finish before the first big one
+    (small jobs never wait behind a big one), and every result equals the job run alone."""
+    from paper_2604_12083_gb300 import mrs
+    srv = mrs.Server(ctx, 1 << 30, 64)
+    try:
+        srv.set_policy(big_job_pairs=1e7, max_big_jobs=1)
+        ra, rb = rod_job(301, 4), rod_job(302, 4)          # 256 nodes, 300 RK2 steps: 3.9e7 pairs
+        vs = [velocity_job(303 + i, 5) for i in range(3)]   # 1280 points: 1.6e6 pairs
+        alone = []
+        for rs in (ra, rb):
+            t, b = run_rod(srv, rs, nsteps=300)
+            srv.drain()
+            alone.append(b[0].cpu().numpy())
+        v_alone = []
+        for p in vs:
+            t, b = run_velocity(srv, p)
+            srv.drain()
+            v_alone.append((b[3].cpu().numpy(), b[4].cpu().numpy()))
+        torch.cuda.synchronize()
+        ta, ba = run_rod(srv, ra, nsteps=300)
+        tb, bb = run_rod(srv, rb, nsteps=300)
+        tv = [run_velocity(srv, p) for p in vs]
+        srv.drain()
+        lat = {t: srv.poll(t)[1] for t in [ta, tb] + [t for t, _ in tv]}
+        # completion times relative to the first submission (submissions are microseconds apart)
+        done_a, done_b = lat[ta], lat[tb]
+        assert done_b - done_a > 0.5 * done_a, (done_a, done_b)      # b waited for a
+        assert all(lat[t] < done_a for t, _ in tv), (lat, done_a)
+        assert rel(ba[0].cpu().numpy() - ra.X, alone[0] - ra.X) < 1e-4
+        assert rel(bb[0].cpu().numpy() - rb.X, alone[1] - rb.X) < 1e-4
+        for (t, b), (u0, w0) in zip(tv, v_alone):
+            assert rel(b[3].cpu().numpy(), u0) < TOL32 and rel(b[4].cpu().numpy(), w0) < TOL32
+        # every job small again: both rod jobs advance together and finish close together
+        srv.set_policy(big_job_pairs=0.0)
+        ta, ba = run_rod(srv, ra, nsteps=300)
+        tb, bb = run_rod(srv, rb, nsteps=300)
+        srv.drain()
+        la, lb = srv.poll(ta)[1], srv.poll(tb)[1]
+        assert abs(lb - la) < 0.5 * la, (la, lb)
+        with pytest.raises(mrs.MrsError):
+            srv.set_policy(1e9, 0)
+    finally:
+        srv.close()
+
+
+def test_injected_allocation_failure(ctx):
+    """A job whose admission fails (allocation failure injected on the host) finishes with
+    MRS_ENOMEM, its buffers untouched; the jobs before and after it complete and match the
+    oracle."""
+    from paper_2604_12083_gb300 import mrs
+    import oracle
+    oracle.build()
+    srv = mrs.Server(ctx, 1 << 30, 1)     # one slot: the velocity jobs wait for the rod job
+    try:
+        rs = rod_job(310, 4)
+        ta, ba = run_rod(srv, rs, nsteps=600)              # ~1200 stages: tens of ms
+        vs = [velocity_job(311 + i, 3) for i in range(3)]
+        tv = [run_velocity(srv, p) for p in vs]
+        srv.inject_alloc_failure(tv[1][0])
+        srv.drain()
+        with pytest.raises(mrs.MrsError) as e:
+            srv.poll(tv[1][0])
+        assert e.value.status == mrs.MRS_ENOMEM and "allocation" in str(e.value)
+        assert torch.isnan(tv[1][1][3]).all() and torch.isnan(tv[1][1][4]).all()
+        for i in (0, 2):
+            p, b = vs[i], tv[i][1]
+            assert srv.poll(tv[i][0])[0]
+            ur, wr = oracle.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+            assert rel(b[3].cpu().numpy(), ur) < TOL32 and rel(b[4].cpu().numpy(), wr) < TOL32
+        assert srv.poll(ta)[0] and torch.isfinite(ba[0]).all()
+        # a job that is no longer waiting cannot be failed
+        with pytest.raises(mrs.MrsError) as e:
+            srv.inject_alloc_failure(ta)
+        assert e.value.status == mrs.MRS_EBUSY
+    finally:
+        srv.close()
