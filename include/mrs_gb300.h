@@ -98,6 +98,19 @@ MRS_API int mrs_ctx_num_sms(const mrs_ctx* ctx);
  * Errors: MRS_EINVAL (mode outside 0..2). */
 MRS_API int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable);
 
+/* Largest column-partial buffer of one pass of a symmetric pair-sum plan (configurations
+ * 17..26; see mrs_plan_create), in bytes, for plans created from then on.  A plan whose column
+ * partials -- 24 bytes per source slot of every work unit, about N^2 / (2 TM) * 24 bytes for one
+ * system of N points -- exceed it runs as several passes of about equal work over consecutive
+ * tiles, each one launch of the pair kernel and one of the reduction kernel, reusing one buffer
+ * (plus 48 bytes per point to carry sums between passes).  Default 256 MiB: the 32768-point
+ * system (34 MB) runs in one pass, a 2^18-point one (2.1 GB) in 9, the 512-system batch of
+ * 256..16384-point systems (515 MB) in 2.  Each further pass costs about 60 us on a GB300 (the
+ * tail of one more persistent launch and one more reduction).  A pass holds at least one tile
+ * row, so its buffer may exceed the setting by up to one row (N / 32 units).  Host only.
+ * Errors: MRS_EINVAL (fewer bytes than one work unit's partials, 768). */
+MRS_API int mrs_ctx_set_sym_pass_bytes(mrs_ctx* ctx, size_t bytes);
+
 /* Device-side anomaly flags raised by the pair-sum kernels of this context since the last call
  * (MRS_FLAG_NONFINITE: a non-finite u or omega was written, e.g. from non-finite inputs).
  * Synchronizes the device, returns the flags in *flags and clears them. */
@@ -183,9 +196,10 @@ MRS_API int mrs_velocity_noalloc(int64_t n_points, const float* X, const float* 
  *           (the kernel values depend on |r| only and the reversed pair has separation -r),
  *           and execution launches the persistent pair kernel plus a small deterministic
  *           reduction kernel; with other targets such a plan runs an ordered configuration.
- *           Their scratch holds one 6-vector per source slot of every work unit (about
+ *           Their column partials hold one 6-vector per source slot of every work unit (about
  *           N^2 / (2 TM) * 24 bytes for one system of N points, TM = threads x points per
- *           thread of the configuration: 384 for the default symmetric one, up to 1536).
+ *           thread of the configuration: 384 for the default symmetric one, up to 1536); beyond
+ *           the context's pass size (mrs_ctx_set_sym_pass_bytes) the plan runs in passes.
  * A plan owns device tables and scratch; mrs_plan_execute allocates nothing and launches one
  * persistent kernel (plus the reduction kernel for a symmetric configuration; for MRS_F64 one
  * plain kernel).  Executions of the same plan must not overlap on the GPU.  Arguments as for
@@ -195,6 +209,10 @@ MRS_API int mrs_plan_create(mrs_ctx* ctx, int n_sys, const int64_t* offsets, dou
 MRS_API int mrs_plan_execute(mrs_plan* plan, const void* X, const void* f, const void* n,
                      const void* Xt, void* u, void* w, void* stream);
 MRS_API int mrs_plan_destroy(mrs_plan* plan);
+/* Passes a plan's execution runs (1 unless a symmetric plan's column partials exceed the
+ * context's pass size) and the bytes of partial-sum scratch it holds.  Either output may be
+ * NULL.  Host only.  Errors: MRS_EINVAL. */
+MRS_API int mrs_plan_scratch(const mrs_plan* plan, int* passes, size_t* scratch_bytes);
 
 /* Autotuner: time every kernel configuration on this batch shape (synthetic inputs generated
  * on the device; temporary buffers allocated and freed here), `reps` timed runs each, and

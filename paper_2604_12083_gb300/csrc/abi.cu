@@ -65,9 +65,8 @@ int default_ordered_config(int n_sys, const int64_t* offsets)
     return 9;
 }
 
-// Symmetric configuration used by default, and the largest scratch it may take by default.
+// Symmetric configuration used by default.
 constexpr int kDefaultSymConfig = 25;
-constexpr double kSymScratchCap = 4.0 * 1024 * 1024 * 1024;
 
 // Work units and column-partial bytes of a symmetric plan with tiles of TM points.
 static double sym_units(int n_sys, const int64_t* offsets, int TM)
@@ -86,8 +85,8 @@ int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precisio
     // Measured on GB300: the symmetric kernel (each unordered pair once) beats the ordered
     // ones when most pairs lie in systems of 8192 points or more and there are enough work
     // units to keep every CTA of the persistent grid busy (a 4096-point system has ~600 units
-    // for ~450 CTAs and runs slower than the ordered kernel).  Its column partials grow as
-    // N^2 / TM, so it is not chosen by default beyond kSymScratchCap of scratch.
+    // for ~450 CTAs and runs slower than the ordered kernel).  Its column partials, which grow
+    // as N^2 / TM, are bounded by splitting the plan into passes (sym_plan_build).
     double big = 0, all = 0;
     for (int s = 0; s < n_sys; ++s) {
         const double ns = (double)(offsets[s + 1] - offsets[s]);
@@ -97,15 +96,14 @@ int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precisio
     const KernelConfig kc = kConfigs[kDefaultSymConfig];
     const double units = sym_units(n_sys, offsets, kc.threads * kc.tpt);
     const double ctas = 3.0 * (ctx ? ctx->num_sms : 152);
-    if (all > 0 && big >= 0.5 * all && units >= 32.0 * ctas &&
-        units * kUnitSources * 6 * sizeof(float) <= kSymScratchCap)
-        return kDefaultSymConfig;
+    if (all > 0 && big >= 0.5 * all && units >= 32.0 * ctas) return kDefaultSymConfig;
     return default_ordered_config(n_sys, offsets);
 }
 
 // Work table of the symmetric path (see SymTile): one row per tile of TM points, from the
-// tile's first point to the end of its system; row segments are numbered tile by tile, one
-// per CTA whose unit range meets the row.
+// tile's first point to the end of its system; the tiles are cut into passes (SymPass) of
+// about equal work whose column partials fit ctx->sym_pass_bytes; within a pass, row segments
+// are numbered tile by tile, one per CTA whose unit range meets the row.
 static int sym_plan_build(mrs_plan* p, mrs_ctx* ctx, int cfg, const int64_t* offsets)
 {
     const KernelConfig kc = kConfigs[cfg];
@@ -136,25 +134,62 @@ static int sym_plan_build(mrs_plan* p, mrs_ctx* ctx, int cfg, const int64_t* off
         set_error("occupancy query failed for config %d", cfg);
         return MRS_ECUDA;
     }
-    long long P = (long long)ctx->num_sms * occ * std::max(1, kc.over);
-    if (P > W) P = W;
-    long long nseg = 0;
-    for (SymTile& T : tiles) {
-        T.qlo = cta_of_unit_host(W, (int)P, T.u0);
-        const int qhi = cta_of_unit_host(W, (int)P, T.u0 + T.nu - 1);
-        T.nseg = qhi - T.qlo + 1;
-        T.seg0 = (int)nseg;
-        nseg += T.nseg;
+    const long long Pmax = (long long)ctx->num_sms * occ * std::max(1, kc.over);
+    // passes: n_pass = ceil(column-partial bytes / sym_pass_bytes); cut at the tile where the
+    // running unit count first reaches g W / n_pass
+    const double unit_bytes = (double)kUnitSources * 6 * sizeof(float);
+    const double cap = std::max<double>((double)ctx->sym_pass_bytes, unit_bytes);
+    const long long n_pass =
+        std::max<long long>(1, (long long)std::ceil((double)W * unit_bytes / cap));
+    p->passes.clear();
+    {
+        const int nt = (int)tiles.size();
+        int ta = 0;
+        for (long long g = 1; g <= n_pass && ta < nt; ++g) {
+            const long long target = (W * g) / n_pass;
+            int tb = ta + 1;
+            while (tb < nt && tiles[tb].u0 < target) ++tb;
+            if (g == n_pass) tb = nt;
+            SymPass ps{};
+            ps.ta = ta;
+            ps.tb = tb;
+            ps.U0 = tiles[ta].u0;
+            ps.W = (tb < nt ? tiles[tb].u0 : W) - ps.U0;
+            const int last_sys = tiles[tb - 1].sys;
+            int tc = tb;
+            while (tc < nt && tiles[tc].sys == last_sys) ++tc;
+            ps.tc = tc;
+            ps.P = (int)std::min<long long>(Pmax, ps.W);
+            p->passes.push_back(ps);
+            ta = tb;
+        }
+    }
+    long long max_seg = 0, max_units = 0, max_P = 0;
+    for (SymPass& ps : p->passes) {
+        long long nseg = 0;
+        for (int t = ps.ta; t < ps.tb; ++t) {
+            SymTile& T = tiles[t];
+            T.qlo = cta_of_unit_host(ps.W, ps.P, T.u0 - ps.U0);
+            const int qhi = cta_of_unit_host(ps.W, ps.P, T.u0 - ps.U0 + T.nu - 1);
+            T.nseg = qhi - T.qlo + 1;
+            T.seg0 = (int)nseg;
+            nseg += T.nseg;
+        }
+        ps.nseg = nseg;
+        max_seg = std::max(max_seg, nseg);
+        max_units = std::max(max_units, ps.W);
+        max_P = std::max<long long>(max_P, ps.P);
     }
     p->sym_config = cfg;
-    p->sP = (int)P;
+    p->sP = (int)max_P;
     p->sW = W;
     p->s_tiles = (int)tiles.size();
     p->sTM = TM;
     if ((st = dev_alloc(&p->d_stiles, tiles.size())) ||
-        (st = dev_alloc(&p->d_rowpart, (size_t)nseg * TM * 6)) ||
-        (st = dev_alloc(&p->d_colpart, (size_t)W * kUnitSources * 6)))
+        (st = dev_alloc(&p->d_rowpart, (size_t)max_seg * TM * 6)) ||
+        (st = dev_alloc(&p->d_colpart, (size_t)max_units * kUnitSources * 6)))
         return st;
+    if (p->passes.size() > 1 && (st = dev_alloc(&p->d_acc, (size_t)p->n_points * 6))) return st;
     cudaMemcpy(p->d_stiles, tiles.data(), tiles.size() * sizeof(SymTile), cudaMemcpyHostToDevice);
     return MRS_OK;
 }
@@ -173,6 +208,7 @@ void plan_free(mrs_plan* p)
     cudaFree(p->d_stiles);
     cudaFree(p->d_rowpart);
     cudaFree(p->d_colpart);
+    cudaFree(p->d_acc);
     delete p;
 }
 
@@ -371,8 +407,6 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
             S.tiles = p->d_stiles;
             S.n_tiles = p->s_tiles;
             S.TM = p->sTM;
-            S.W = p->sW;
-            S.P = p->sP;
             S.sc = p->d_sc;
             S.X = L.X;
             S.f = L.f;
@@ -381,8 +415,19 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
             S.w = L.w;
             S.rowpart = p->d_rowpart;
             S.colpart = p->d_colpart;
+            S.acc = p->d_acc;
             S.err = L.err;
-            e = launch_mrs_sym(p->sym_config, p->precision == MRS_F32_COMP, S, s);
+            e = cudaSuccess;
+            for (const SymPass& ps : p->passes) {   // in order: each pass reuses the buffers
+                S.W = ps.W;
+                S.P = ps.P;
+                S.U0 = ps.U0;
+                S.ta = ps.ta;
+                S.tb = ps.tb;
+                S.tc = ps.tc;
+                e = launch_mrs_sym(p->sym_config, p->precision == MRS_F32_COMP, S, s);
+                if (e != cudaSuccess) break;
+            }
         } else {
             e = launch_mrs_f32(p->ocfg, p->precision == MRS_F32_COMP, L, s);
         }
@@ -461,6 +506,17 @@ int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable)
     return MRS_OK;
 }
 
+int mrs_ctx_set_sym_pass_bytes(mrs_ctx* ctx, size_t bytes)
+{
+    clear_error();
+    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+    MRS_REQUIRE(bytes >= (size_t)kUnitSources * 6 * sizeof(float),
+                "bytes must hold at least one work unit's column partials (%zu)",
+                (size_t)kUnitSources * 6 * sizeof(float));
+    ctx->sym_pass_bytes = bytes;
+    return MRS_OK;
+}
+
 int mrs_device_status(mrs_ctx* ctx, unsigned int* flags)
 {
     clear_error();
@@ -530,6 +586,29 @@ int mrs_plan_info(const mrs_plan* plan, int* grid, int64_t* work_units, int* con
     if (grid) *grid = plan->precision == MRS_F64 ? plan->n_blocks64 : (sym ? plan->sP : plan->P);
     if (work_units) *work_units = sym ? plan->sW : plan->W;
     if (config) *config = plan->config;
+    return MRS_OK;
+}
+
+int mrs_plan_scratch(const mrs_plan* plan, int* passes, size_t* scratch_bytes)
+{
+    clear_error();
+    MRS_REQUIRE(plan != nullptr, "plan is NULL");
+    const bool sym = plan->precision != MRS_F64 && plan->sym_config >= 0;
+    if (passes) *passes = sym ? (int)plan->passes.size() : 1;
+    if (scratch_bytes) {
+        size_t b = (size_t)2 * plan->P * 6 * plan->TM * sizeof(float);   // ordered slots
+        if (sym) {
+            long long seg = 0, units = 0;
+            for (const SymPass& ps : plan->passes) {
+                seg = std::max(seg, ps.nseg);
+                units = std::max(units, ps.W);
+            }
+            b += (size_t)seg * plan->sTM * 6 * sizeof(float) +
+                 (size_t)units * kUnitSources * 6 * sizeof(float) +
+                 (plan->passes.size() > 1 ? (size_t)plan->n_points * 6 * sizeof(float2) : 0);
+        }
+        *scratch_bytes = b;
+    }
     return MRS_OK;
 }
 

@@ -135,6 +135,14 @@ int occupancy_f32(int config, bool comp, int* ctas_per_sm);
 // the contiguous unit range [W p / P, W (p+1) / P).  Every segment of a row processed by one
 // CTA writes a row partial; a second kernel sums, for every point, its row partials and the
 // column partials of all earlier tiles of its system in a fixed order (deterministic).
+//
+// Passes: the column partials (one 6-vector per source slot of every unit, ~N^2 / (2 TM) of
+// them) are bounded by cutting the tile list into consecutive passes of about equal work, each
+// one launch of the pair kernel over its own units and one of the reduction kernel, which
+// reuse one column-partial buffer of the largest pass's size.  A point's sum is final after
+// the pass holding its tile (later passes only hold later tiles, whose column partials go to
+// later points); the reduction of a pass writes the final values of its own tiles and carries
+// the Kahan pair of every later point of the systems it touches to the next pass in `acc`.
 // ---------------------------------------------------------------------------------------------
 constexpr int kSymChunk = 128;     // sources staged in shared memory at a time
 
@@ -149,17 +157,29 @@ struct SymTile {
     int tfirst;    // global index of the system's first tile
     int seg0;      // first row-partial slot of this tile
     int nseg;      // number of CTAs (row segments) that process this row
-    int qlo;       // first CTA whose unit range meets the row
+    int qlo;       // first CTA (of the tile's pass) whose unit range meets the row
     int pad_;
     long long u0;  // global index of the row's first unit
+};
+
+// One pass of a symmetric plan: tiles [ta, tb) and their units [U0, U0 + W), run by P CTAs;
+// the reduction covers tiles [ta, tc), tc = the end of the system of tile tb - 1.  seg0 and
+// qlo of its tiles count from the pass's first row segment and first CTA.
+struct SymPass {
+    int ta, tb, tc, P;
+    long long U0, W;
+    long long nseg;       // row segments of the pass
 };
 
 struct SymLaunch {
     const SymTile* tiles;
     int n_tiles;
     int TM;
-    long long W;          // total work units
+    long long W;          // work units of this pass
     int P;                // persistent CTAs
+    long long U0;         // first work unit of this pass (global unit index; 0: one pass)
+    int ta, tb, tc;       // tiles of this pass [ta, tb); the reduction covers tiles [ta, tc)
+    float2* acc;          // [points][6] Kahan pairs carried between passes (NULL: one pass)
     const SysConst* sc;
     const float* X;
     const float* f;
@@ -167,7 +187,7 @@ struct SymLaunch {
     float* u;
     float* w;
     float* rowpart;       // [segments][TM][6]
-    float* colpart;       // [W * kUnitSources][6]: unit-major, one 6-vector per source slot
+    float* colpart;       // [W * kUnitSources][6]: unit-major from U0, one 6-vector per source slot
     unsigned int* err;
 };
 
@@ -245,9 +265,11 @@ struct mrs_plan {
     int sTM = 0;
     long long sW = 0;
     int s_tiles = 0;
+    std::vector<mrs::SymPass> passes;
     mrs::SymTile* d_stiles = nullptr;
     float* d_rowpart = nullptr;
     float* d_colpart = nullptr;
+    float2* d_acc = nullptr;      // Kahan pairs carried between passes (more than one pass)
     // float64 path
     long long* d_off64 = nullptr;
     double* d_eps64 = nullptr;
@@ -274,6 +296,9 @@ struct mrs_ctx {
     // rod stepping in one fused launch per call (mrs_ctx_set_fused_steps): 0 never, 1 for
     // instances of at most kFusedAutoNodes nodes, 2 whenever the instance fits shared memory
     int fused_steps = 1;
+    // largest column-partial buffer (bytes) of one pass of a symmetric plan; a plan with more
+    // column partials is split into passes (mrs_ctx_set_sym_pass_bytes)
+    size_t sym_pass_bytes = (size_t)256 << 20;
 };
 
 namespace mrs {

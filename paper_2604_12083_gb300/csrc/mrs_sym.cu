@@ -179,13 +179,13 @@ mrs_f32_sym(const SymLaunch L)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = blockIdx.x;
-    long long ubeg = unit_start(L.W, L.P, p);
-    const long long uend = unit_start(L.W, L.P, p + 1);
+    long long ubeg = L.U0 + unit_start(L.W, L.P, p);
+    const long long uend = L.U0 + unit_start(L.W, L.P, p + 1);
     if (ubeg >= uend) return;
 
     int ti;
     {
-        int lo = 0, hi = L.n_tiles - 1;
+        int lo = L.ta, hi = L.tb - 1;   // the pass's tiles
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (L.tiles[mid].u0 <= ubeg) lo = mid; else hi = mid - 1;
@@ -327,7 +327,7 @@ mrs_f32_sym(const SymLaunch L)
             if (!diag) {
                 __syncthreads();
                 // column partials of this chunk: the sum over the CTA's warps, in warp order
-                float* cp = L.colpart + ((long long)T.u0 * kUnitSources + (j0 - T.t0)) * 6;
+                float* cp = L.colpart + ((T.u0 - L.U0) * kUnitSources + (j0 - T.t0)) * 6;
                 for (int idx = tid; idx < cnt * 6; idx += BLOCK) {
                     // idx = 6 j + q; SKEW keeps the partials component-major
                     const int sidx = SKEW ? (idx % 6) * CH + idx / 6 : idx;
@@ -383,38 +383,56 @@ mrs_f32_sym(const SymLaunch L)
     }
 }
 
-// Final sum per point and component: its row's partials (CTA order), then the column partials
-// of every earlier tile of its system (tile order), Kahan-compensated; scaled by 1/(8 pi mu).
-// One thread per (point, component), so consecutive threads read consecutive floats; the
-// partials are fetched kRedAhead at a time so that their L2 latencies overlap.
+// Sum per point and component over one pass: the Kahan pair carried from earlier passes (none
+// in the first pass touching the point's system), then -- for a point of the pass's own tiles
+// -- its row's partials (CTA order) and the column partials of the earlier tiles of its system
+// that lie in the pass (tile order); for a later point of a system the pass touches, the
+// column partials of all the pass's tiles of that system.  Own points are final: scaled by
+// 1/(8 pi mu) and written out; later points carry their pair to the next pass.  With one pass
+// this is rows then every earlier tile's column partial, from a zero pair.  One thread per
+// (point, component), so consecutive threads read consecutive floats; the partials are
+// fetched kRedAhead at a time so that their L2 latencies overlap.
 constexpr int kRedAhead = 8;
 
 __global__ void __launch_bounds__(256) mrs_sym_reduce(const SymLaunch L)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)L.n_tiles * L.TM * 6) return;
+    if (idx >= (long long)(L.tc - L.ta) * L.TM * 6) return;
     const long long pt = idx / 6;
     const int q = (int)(idx - pt * 6);
-    const int ti = (int)(pt / L.TM), li = (int)(pt - (long long)ti * L.TM);
+    const int tl = (int)(pt / L.TM), li = (int)(pt - (long long)tl * L.TM);
+    const int ti = L.ta + tl;
     const SymTile T = L.tiles[ti];
     if (li >= T.tn) return;
     const int j = T.t0 + li;
+    const bool own = ti < L.tb;
     float sum = 0.f, cmp = 0.f;
-    for (int sgi = 0; sgi < T.nseg; ++sgi)
-        kahan_add(sum, cmp, __ldcg(L.rowpart + ((long long)(T.seg0 + sgi) * L.TM + li) * 6 + q));
-    for (int k0 = 0; k0 < T.kt; k0 += kRedAhead) {
+    if (T.tfirst < L.ta) {   // an earlier pass holds tiles of this system: its carried pair
+        const float2 a = L.acc[(long long)j * 6 + q];
+        sum = a.x;
+        cmp = a.y;
+    }
+    if (own)
+        for (int sgi = 0; sgi < T.nseg; ++sgi)
+            kahan_add(sum, cmp, __ldcg(L.rowpart + ((long long)(T.seg0 + sgi) * L.TM + li) * 6 + q));
+    const int c0 = max(T.tfirst, L.ta), c1 = own ? ti : L.tb;   // column tiles [c0, c1)
+    for (int k0 = c0; k0 < c1; k0 += kRedAhead) {
         float v[kRedAhead];
 #pragma unroll
         for (int a = 0; a < kRedAhead; ++a) {
             v[a] = 0.f;
-            if (k0 + a < T.kt) {
-                const SymTile& R = L.tiles[T.tfirst + k0 + a];
-                v[a] = __ldcg(L.colpart + ((long long)R.u0 * kUnitSources + (j - R.t0)) * 6 + q);
+            if (k0 + a < c1) {
+                const SymTile& R = L.tiles[k0 + a];
+                v[a] = __ldcg(L.colpart + ((R.u0 - L.U0) * kUnitSources + (j - R.t0)) * 6 + q);
             }
         }
 #pragma unroll
         for (int a = 0; a < kRedAhead; ++a)
-            if (k0 + a < T.kt) kahan_add(sum, cmp, v[a]);
+            if (k0 + a < c1) kahan_add(sum, cmp, v[a]);
+    }
+    if (!own) {
+        L.acc[(long long)j * 6 + q] = make_float2(sum, cmp);
+        return;
     }
     const float val = __fsub_rn(sum, cmp) * L.sc[T.sys].scale;
     if (!isfinite(val)) atomicOr(L.err, 1u);
@@ -449,7 +467,8 @@ static cudaError_t launch_sym_t(const SymLaunch& L, cudaStream_t s)
         <<<L.P, BLOCK, sym_smem_bytes<BLOCK, TPT, COMP>(), s>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const long long n = (long long)L.n_tiles * L.TM * 6;
+    const long long n = (long long)(L.tc - L.ta) * L.TM * 6;
+    if (n == 0) return cudaSuccess;
     mrs_sym_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L);
     return cudaGetLastError();
 }

@@ -430,6 +430,11 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
         L.TM = S->sTM;
         L.W = sW;
         L.P = sP;
+        L.U0 = 0;                 // one pass over every tile of the iteration
+        L.ta = 0;
+        L.tb = snt;
+        L.tc = snt;
+        L.acc = nullptr;
         L.sc = S->d_sc;
         L.X = S->pX;
         L.f = S->pf;

@@ -27,9 +27,10 @@ STATUS_NAMES = {0: "MRS_OK", 1: "MRS_EINVAL", 2: "MRS_ENOMEM", 3: "MRS_ECUDA", 4
 # Every symbol include/mrs_gb300.h declares (kept in sync by tests/test_abi.py).
 EXPORTS = [
     "mrs_last_error", "mrs_version", "mrs_ctx_create", "mrs_ctx_destroy", "mrs_ctx_num_sms",
-    "mrs_ctx_set_fused_steps",
+    "mrs_ctx_set_fused_steps", "mrs_ctx_set_sym_pass_bytes",
     "mrs_velocity", "mrs_plan_create", "mrs_plan_execute", "mrs_plan_destroy",
     "mrs_plan_config_count", "mrs_plan_config_symmetric", "mrs_plan_config_info", "mrs_plan_info",
+    "mrs_plan_scratch",
     "rod_forces", "rod_step", "rot_sqrt_batch", "parareal_run", "mrs_velocity_noalloc",
     "serve_create", "serve_submit", "serve_poll", "serve_drain", "serve_stats", "serve_destroy",
     "serve_set_policy", "serve_inject_alloc_failure",
@@ -111,6 +112,7 @@ def lib():
         L.mrs_ctx_destroy.argtypes = [_vp]
         L.mrs_ctx_num_sms.argtypes = [_vp]
         L.mrs_ctx_set_fused_steps.argtypes = [_vp, ctypes.c_int]
+        L.mrs_ctx_set_sym_pass_bytes.argtypes = [_vp, ctypes.c_size_t]
         L.mrs_device_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint)]
         L.mrs_velocity.argtypes = [_vp, ctypes.c_int, _i64p, _vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _vp]
@@ -122,6 +124,7 @@ def lib():
         L.mrs_plan_destroy.argtypes = [_vp]
         L.mrs_plan_config_info.argtypes = [_vp, ctypes.c_int, _ip, _ip, _ip]
         L.mrs_plan_info.argtypes = [_vp, _ip, _i64p, _ip]
+        L.mrs_plan_scratch.argtypes = [_vp, _ip, ctypes.POINTER(ctypes.c_size_t)]
         L.rod_forces.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.POINTER(RodParams), _vp, _vp,
                                  ctypes.c_double, _vp, _vp, _vp]
         L.rod_step.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.POINTER(RodParams), _vp, _vp,
@@ -198,6 +201,11 @@ class Context:
     def num_sms(self) -> int:
         return int(lib().mrs_ctx_num_sms(self.handle))
 
+    def set_sym_pass_bytes(self, nbytes: int) -> None:
+        """``mrs_ctx_set_sym_pass_bytes``: column-partial buffer of one pass of a symmetric plan
+        (plans created afterwards; larger plans run in several passes)."""
+        _check(lib().mrs_ctx_set_sym_pass_bytes(self.handle, int(nbytes)))
+
     def set_fused_steps(self, mode: int) -> None:
         """``mrs_ctx_set_fused_steps``: 1 (default) one fused launch per rod-stepping call for
         instances of at most 128 nodes, 2 whenever the instance fits shared memory, 0 never."""
@@ -272,6 +280,12 @@ class Plan:
     def execute(self, X, f, n, u, w, Xt=None, stream=None):
         _check(lib().mrs_plan_execute(self.handle, _ptr(X), _ptr(f), _ptr(n), _ptr(Xt), _ptr(u),
                                       _ptr(w), _stream(stream)))
+
+    def scratch(self):
+        """``mrs_plan_scratch``: {"passes": executions' passes, "bytes": partial-sum scratch}."""
+        npass, nbytes = ctypes.c_int(), ctypes.c_size_t()
+        _check(lib().mrs_plan_scratch(self.handle, ctypes.byref(npass), ctypes.byref(nbytes)))
+        return {"passes": npass.value, "bytes": nbytes.value}
 
     def info(self):
         g, c = ctypes.c_int(), ctypes.c_int()

@@ -373,10 +373,12 @@ def test_nonfinite_inputs_raise_the_device_flag(ctx):
         assert ctx.device_status() == 0
 
 
-@pytest.mark.parametrize("config", [None, 17])
+@pytest.mark.parametrize("config", [-1, 8])
 def test_large_ragged_single_system_sampled(ctx, orc, config):
-    """2^18 + 17 points (6.9e10 pairs, a ragged last tile): 256 sampled targets against all
-    sources, computed one by one by the oracle."""
+    """2^18 + 17 points (6.9e10 pairs, a ragged last tile): the library's choice -- the
+    symmetric kernel, its column partials (2.1 GB in one pass) split into passes -- and an
+    ordered configuration; 256 sampled targets (incl. the last tile) against all sources,
+    computed one by one by the oracle."""
     from paper_2604_12083_gb300 import mrs, workloads as W
     rng = np.random.default_rng(68)
     N = (1 << 18) + 17
@@ -384,10 +386,75 @@ def test_large_ragged_single_system_sampled(ctx, orc, config):
     f = rng.standard_normal((N, 3)).astype(np.float32)
     n = rng.standard_normal((N, 3)).astype(np.float32)
     p = W.MRSProblem("large", np.array([0, N], np.int64), X, f, n, np.array([0.02]), 1.0)
-    u, w = run(ctx, p, mrs.MRS_F32_COMP, config=config)
+    pl = mrs.Plan(ctx, p.offsets, p.mu, 0.02, precision=mrs.MRS_F32_COMP, config=config)
+    sc = pl.scratch()
+    if config == -1:
+        assert mrs.plan_config_symmetric(pl.info()["config"])
+        assert sc["passes"] > 1 and sc["bytes"] <= 320 << 20, sc
+    Xd, fd, nd = dev(p.X), dev(p.f), dev(p.n)
+    ud, wd = torch.full_like(Xd, float("nan")), torch.full_like(Xd, float("nan"))
+    pl.execute(Xd, fd, nd, ud, wd)
+    torch.cuda.synchronize()
+    pl.close()
+    u, w = ud.double().cpu().numpy(), wd.double().cpu().numpy()
+    assert np.isfinite(u).all() and np.isfinite(w).all()
     idx = np.concatenate([rng.choice(N, 250, replace=False), np.arange(N - 6, N)])
     ur, wr = orc.mrs_velocity(p.X, p.f, p.n, 0.02, 1.0, xt=p.X[idx])
     assert rel_l2(u[idx], ur) < TOL32 and rel_l2(w[idx], wr) < TOL32
+    assert per_target_max(u[idx], ur) < PER_TARGET and per_target_max(w[idx], wr) < PER_TARGET
+
+
+def run_with_pass_bytes(ctx, p, precision, config, nbytes):
+    """Plan built with a column-partial buffer of nbytes per pass; returns (u, w, passes)."""
+    from paper_2604_12083_gb300 import mrs
+    ctx.set_sym_pass_bytes(nbytes)
+    try:
+        pl = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=precision,
+                      config=config)
+    finally:
+        ctx.set_sym_pass_bytes(256 << 20)
+    X, f, n = dev(p.X), dev(p.f), dev(p.n)
+    out = []
+    for _ in range(2):
+        u, w = torch.full_like(X, float("nan")), torch.full_like(X, float("nan"))
+        pl.execute(X, f, n, u, w)
+        torch.cuda.synchronize()
+        out.append((u.double().cpu().numpy(), w.double().cpu().numpy()))
+    npass = pl.scratch()["passes"]
+    pl.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    return out[0][0], out[0][1], npass
+
+
+@pytest.mark.parametrize("config", [17, 20, 25, 26])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_symmetric_passes_match_oracle(ctx, mid_system, config, precision):
+    """A symmetric plan of the 20000-point system split into passes (a 256 KiB column-partial
+    buffer: dozens of passes, cut inside the system) gives the oracle's result, as one pass
+    does, bit-identically on repeated calls."""
+    p, ur, wr = mid_system
+    u1, w1, n1 = run_with_pass_bytes(ctx, p, precision, config, 256 << 20)
+    u, w, npass = run_with_pass_bytes(ctx, p, precision, config, 256 << 10)
+    assert n1 == 1 and npass > 10, (n1, npass)
+    assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
+    assert per_target_max(u, ur) < PER_TARGET and per_target_max(w, wr) < PER_TARGET
+    assert rel_l2(u, u1) < TOL32 and rel_l2(w, w1) < TOL32
+
+
+@pytest.mark.parametrize("config", list(range(17, N_CONFIGS)))
+def test_symmetric_passes_ragged_batch(ctx, orc, config):
+    """The ragged batch with passes of three work units: passes end inside systems, span
+    several small systems and hold single tiles; every system matches the oracle."""
+    from paper_2604_12083_gb300 import mrs
+    p = ragged_batch()
+    u, w, npass = run_with_pass_bytes(ctx, p, mrs.MRS_F32_COMP, config, 3 * 768)
+    assert npass >= 10, npass
+    ur, wr = orc.mrs_velocity_batch(p.offsets, p.X, p.f, p.n, 0.0, p.mu, eps_per_sys=p.eps)
+    for s in range(len(p.offsets) - 1):
+        a, b = p.offsets[s], p.offsets[s + 1]
+        if a < b:
+            assert rel_l2(u[a:b], ur[a:b]) < TOL32, (s, b - a)
+            assert rel_l2(w[a:b], wr[a:b]) < TOL32, (s, b - a)
 
 
 @pytest.mark.parametrize("config", [8, 25, 26])
