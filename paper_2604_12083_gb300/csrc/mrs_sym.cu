@@ -388,48 +388,65 @@ mrs_f32_sym(const SymLaunch L)
 // -- its row's partials (CTA order) and the column partials of the earlier tiles of its system
 // that lie in the pass (tile order); for a later point of a system the pass touches, the
 // column partials of all the pass's tiles of that system.  Own points are final: scaled by
-// 1/(8 pi mu) and written out; later points carry their pair to the next pass.  With one pass
-// this is rows then every earlier tile's column partial, from a zero pair.  One thread per
-// (point, component), so consecutive threads read consecutive floats; the partials are
-// fetched kRedAhead at a time so that their L2 latencies overlap.
+// 1/(8 pi mu) and written out; later points carry their pair to the next pass.
+// kRedSplit consecutive lanes share one (point, component): lane r sums the terms r, r + R,
+// r + 2R, ... of that sequence into its own Kahan pair (lane 0 starting from the carried
+// pair), fetching kRedAhead terms at a time so that their L2 latencies overlap, and lane 0
+// then adds the other lanes' compensated sums in lane order -- a fixed order, so the result
+// is deterministic.
 constexpr int kRedAhead = 8;
+constexpr int kRedSplit = 4;
 
 __global__ void __launch_bounds__(256) mrs_sym_reduce(const SymLaunch L)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)(L.tc - L.ta) * L.TM * 6) return;
-    const long long pt = idx / 6;
-    const int q = (int)(idx - pt * 6);
+    if (idx >= (long long)(L.tc - L.ta) * L.TM * 6 * kRedSplit) return;   // whole lane groups
+    const int r = (int)(idx % kRedSplit);
+    const long long pq = idx / kRedSplit;
+    const long long pt = pq / 6;
+    const int q = (int)(pq - pt * 6);
     const int tl = (int)(pt / L.TM), li = (int)(pt - (long long)tl * L.TM);
     const int ti = L.ta + tl;
     const SymTile T = L.tiles[ti];
-    if (li >= T.tn) return;
+    if (li >= T.tn) return;   // the whole lane group leaves together
     const int j = T.t0 + li;
     const bool own = ti < L.tb;
     float sum = 0.f, cmp = 0.f;
-    if (T.tfirst < L.ta) {   // an earlier pass holds tiles of this system: its carried pair
+    if (r == 0 && T.tfirst < L.ta) {   // an earlier pass holds tiles of this system
         const float2 a = L.acc[(long long)j * 6 + q];
         sum = a.x;
         cmp = a.y;
     }
-    if (own)
-        for (int sgi = 0; sgi < T.nseg; ++sgi)
-            kahan_add(sum, cmp, __ldcg(L.rowpart + ((long long)(T.seg0 + sgi) * L.TM + li) * 6 + q));
+    const int nrow = own ? T.nseg : 0;
     const int c0 = max(T.tfirst, L.ta), c1 = own ? ti : L.tb;   // column tiles [c0, c1)
-    for (int k0 = c0; k0 < c1; k0 += kRedAhead) {
+    const int nterm = nrow + max(0, c1 - c0);
+    for (int k0 = r; k0 < nterm; k0 += kRedSplit * kRedAhead) {
         float v[kRedAhead];
 #pragma unroll
         for (int a = 0; a < kRedAhead; ++a) {
+            const int k = k0 + a * kRedSplit;
             v[a] = 0.f;
-            if (k0 + a < c1) {
-                const SymTile& R = L.tiles[k0 + a];
+            if (k < nrow) {
+                v[a] = __ldcg(L.rowpart + ((long long)(T.seg0 + k) * L.TM + li) * 6 + q);
+            } else if (k < nterm) {
+                const SymTile& R = L.tiles[c0 + (k - nrow)];
                 v[a] = __ldcg(L.colpart + ((R.u0 - L.U0) * kUnitSources + (j - R.t0)) * 6 + q);
             }
         }
 #pragma unroll
         for (int a = 0; a < kRedAhead; ++a)
-            if (k0 + a < c1) kahan_add(sum, cmp, v[a]);
+            if (k0 + a * kRedSplit < nterm) kahan_add(sum, cmp, v[a]);
     }
+    // lane 0 of the group folds in lanes 1..R-1, in lane order
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned mask = ((1u << kRedSplit) - 1u) << (lane & ~(unsigned)(kRedSplit - 1));
+    float part = __fsub_rn(sum, cmp);
+#pragma unroll
+    for (int o = 1; o < kRedSplit; ++o) {
+        const float other = __shfl_down_sync(mask, part, o, kRedSplit);
+        if (r == 0) kahan_add(sum, cmp, other);
+    }
+    if (r != 0) return;
     if (!own) {
         L.acc[(long long)j * 6 + q] = make_float2(sum, cmp);
         return;
@@ -467,7 +484,7 @@ static cudaError_t launch_sym_t(const SymLaunch& L, cudaStream_t s)
         <<<L.P, BLOCK, sym_smem_bytes<BLOCK, TPT, COMP>(), s>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const long long n = (long long)(L.tc - L.ta) * L.TM * 6;
+    const long long n = (long long)(L.tc - L.ta) * L.TM * 6 * kRedSplit;
     if (n == 0) return cudaSuccess;
     mrs_sym_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L);
     return cudaGetLastError();
