@@ -432,6 +432,99 @@ def extra_parareal(ctx, dev):
     return out
 
 
+def run_fp32_peak(args):
+    """The FP32 FMA pipe's throughput on this GPU (mrs_fma_probe): scalar FFMA, packed FFMA2 and
+    the two interleaved, against the nominal 2 x 128 lanes x SMs x maximum SM clock, with the SM
+    clock sampled during the runs."""
+    import torch
+    from paper_2604_12083_gb300 import build as B, mrs
+    B.build()
+    torch.cuda.init()
+    clk = ClockSampler(0)
+    clk.start()
+    res = {}
+    for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "ffma_ffma2_interleaved")):
+        best = None
+        for _ in range(5):
+            tf, ms = mrs.fma_probe(0, kind, 1 << 18)
+            if best is None or tf > best[0]:
+                best = (tf, ms)
+        res[name] = {"tflops": best[0], "ms": best[1]}
+    clocks = clk.stop()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = 2 * 128 * sms * float(load_peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    for v in res.values():
+        v["frac_of_nominal"] = v["tflops"] / peak
+    print(json.dumps({"case": "fp32_peak", "nominal_tflops": peak, "sms": sms,
+                      "nominal_basis": "2 x 128 FP32 lanes x SMs x max SM clock", **res,
+                      "clocks": clocks}), flush=True)
+
+
+def run_parareal_horizon(args):
+    """The Parareal configuration at its configured horizon: 8 filaments x 512 nodes (seed 4),
+    64 slices over T = 1/horizon of a beat period (the wave frequency f = 2 pi makes one
+    period one time unit), fine RK2 at dt = 1e-6, coarse Euler at 16 dt.  A slice holds a whole
+    number of coarse steps, so T = 64 x floor(10^6 / (64 horizon) / 16) x 16 dt (1/16 period:
+    976 fine steps per slice, T = 0.062464, 0.9994 of it).  Serial fine RK2 over [0, T] on the
+    same GPU is the reference: reported are its wall time, and for the regular and the pipelined
+    Parareal schedule the wall time, iterations, the increment series (Eq. true_err's
+    increment) and the final state's error against serial fine (Eq. true_err at T)."""
+    import torch
+    from paper_2604_12083_gb300 import build as B, mrs, workloads as W
+    B.build()
+    dev = torch.device("cuda", 0)
+    ctx = mrs.Context(0)
+    rs = W.rod_system(4, 8, 512)
+    c = W.ROD_PARAREAL
+    prm = mrs.RodParams.make(c["L"], c["a"], c["b"], c["wave_A"], c["wave_k"], c["wave_f"], 1.0, rs.eps)
+    Ns, r, dt = 64, 16, c["dt"]
+    nf = int(1e6 / (Ns * args.horizon) / r) * r
+    T1 = Ns * nf * dt
+    tol, max_iter = args.tol, args.max_iter
+    fresh = lambda: (torch.from_numpy(rs.X.copy()).to(dev), torch.from_numpy(rs.D.copy()).to(dev))
+    # warm-up: workspaces, captured graphs and plans of both schedules (a short horizon)
+    Xw, Dw = fresh()
+    mrs.rod_step(ctx, rs.rod_off, prm, Xw, Dw, 0.0, dt, 2 * r, mrs.MRS_RK2)
+    for gs in (0, 8):
+        Xw, Dw = fresh()
+        mrs.parareal_run(ctx, rs.rod_off, prm, Xw, Dw, 0.0, Ns * r * dt, Ns, dt, r, 2, tol,
+                         raise_on_noconv=False, group_size=gs)
+    Xs, Ds = fresh()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mrs.rod_step(ctx, rs.rod_off, prm, Xs, Ds, 0.0, dt, Ns * nf, mrs.MRS_RK2)
+    torch.cuda.synchronize()
+    t_serial = time.perf_counter() - t0
+    xs = Xs.cpu().numpy()
+
+    def true_err(x):
+        return float(np.max(np.linalg.norm(x - xs, axis=1) / np.linalg.norm(xs, axis=1)))
+
+    out = {"case": "parareal_horizon",
+           "workload": "8 filaments x 512 nodes (4096 points), 64 slices x %d fine RK2 steps "
+                       "(dt = 1e-6), coarse Euler 16 dt, T = %.6f (1/%g of a beat period)"
+                       % (nf, T1, args.horizon),
+           "tol": tol, "max_iter": max_iter, "serial_fine_s": t_serial,
+           "serial_fine_steps": Ns * nf, "runs": []}
+    for gs in (0, 8):
+        Xp, Dp = fresh()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = mrs.parareal_run(ctx, rs.rod_off, prm, Xp, Dp, 0.0, T1, Ns, dt, r, max_iter, tol,
+                              raise_on_noconv=False, group_size=gs)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out["runs"].append({
+            "schedule": "pipelined (groups of 8)" if gs else "regular",
+            "iterations": st.iterations, "seconds": wall, "converged": bool(st.final_incr < tol),
+            "increments": [st.incr[i] for i in range(st.iterations)],
+            "fine_steps_executed": st.fine_steps, "coarse_steps_executed": st.coarse_steps,
+            "final_state_true_err": true_err(Xp.cpu().numpy()),
+            "speedup_vs_serial_fine": t_serial / wall})
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def _serve_jobs(trace, dev, seed):
     """Device buffers for every job of a trace (built before any timing)."""
     import torch
@@ -981,14 +1074,20 @@ def main():
     ap.add_argument("--config", type=int, default=-1,
                     help="force this pair-sum plan configuration (default: the library's choice)")
     ap.add_argument("--case", choices=["main", "rod_kernels", "parareal", "small_systems",
-                                       "paper_sizes", "batch", "serve"],
+                                       "paper_sizes", "batch", "serve", "parareal_horizon", "fp32_peak"],
                     default="main",
                     help="rod_kernels: time the rod force and update kernels on 1M nodes; "
                          "parareal: the Parareal measurements alone; small_systems: latency of "
                          "one pair sum on single systems of 1k..16k points; paper_sizes: "
                          "per-call latency at the paper's own sizes (1..25 rods of 51 points); "
                          "batch: the 512-system batch alone (--config to skip autotuning); "
-                         "serve: the serving measurements alone")
+                         "serve: the serving measurements alone; parareal_horizon: Parareal "
+                         "at 1/--horizon of a beat period against serial fine stepping")
+    ap.add_argument("--horizon", type=float, default=16.0,
+                    help="parareal_horizon: T = 1/horizon of a beat period (1: the full period)")
+    ap.add_argument("--tol", type=float, default=1e-11, help="parareal_horizon: increment tolerance")
+    ap.add_argument("--max-iter", dest="max_iter", type=int, default=16,
+                    help="parareal_horizon: iteration cap")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1009,6 +1108,12 @@ def main():
         return
     if args.case == "batch":
         run_batch_case(args)
+        return
+    if args.case == "parareal_horizon":
+        run_parareal_horizon(args)
+        return
+    if args.case == "fp32_peak":
+        run_fp32_peak(args)
         return
     if args.case == "serve":
         import torch

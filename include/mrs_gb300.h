@@ -111,6 +111,15 @@ MRS_API int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable);
  * Errors: MRS_EINVAL (fewer bytes than one work unit's partials, 768). */
 MRS_API int mrs_ctx_set_sym_pass_bytes(mrs_ctx* ctx, size_t bytes);
 
+/* Measurement aid (the paper has no counterpart): FP32 FMA-pipe throughput of the device, in
+ * TFLOP/s (2 flops per lane FMA), for kind 0: scalar FFMA, 1: packed FFMA2 (fma.rn.f32x2, the
+ * form the pair-sum kernels use), 2: the two interleaved.  One launch of every resident
+ * thread running 8 independent chains of `iters` steps (two lane FMAs per chain and step),
+ * timed with CUDA events after a warm-up launch; *ms (may be NULL) gets the launch's time.
+ * Allocates and frees a small buffer and synchronizes the device.
+ * Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */
+MRS_API int mrs_fma_probe(int device, int kind, int iters, double* tflops, float* ms);
+
 /* Device-side anomaly flags raised by the pair-sum kernels of this context since the last call
  * (MRS_FLAG_NONFINITE: a non-finite u or omega was written, e.g. from non-finite inputs).
  * Synchronizes the device, returns the flags in *flags and clears them. */
@@ -344,10 +353,10 @@ MRS_API int parareal_run(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const
  * serial coarse/correction sweep with fine work.  The next iteration's fine solves are queued
  * before the current increment is known; if the current iteration converges, that work is
  * discarded.  When the fine solves of all slices fill the GPU (n_points x n_slices >= 65536)
- * and, from the third iteration on, the last two increments extrapolate geometrically below
- * tol, the current increment is read first and the next fine solves are queued only if
- * needed.  All ordering is by CUDA events between streams (no device-side
- * waiting).
+ * and either (second iteration) the first increment is below 1000 tol or (from the third
+ * iteration on) the last two increments extrapolate geometrically below tol, the current
+ * increment is read first and the next fine solves are queued only if needed.  All ordering
+ * is by CUDA events between streams (no device-side waiting).
  * Arguments, outputs and errors as for parareal_run; group_size in 1..n_slices. */
 MRS_API int parareal_run_pipelined(mrs_ctx* ctx, int n_rods, const int64_t* rod_off,
                                    const mrs_rod_params* p, double* X, double* D, double T0,

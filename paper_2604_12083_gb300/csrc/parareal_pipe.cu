@@ -18,8 +18,10 @@
 // kSpecPoints points per batched stage), discarded speculative work costs real time, so
 // speculation is skipped when the increments so far predict that iteration k converges
 // (eta~^{k-1} * (eta~^{k-1} / eta~^{k-2}) < tol, the geometric trend of the last two
-// increments): the host then reads eta~^k first and enqueues the fine solves of iteration k+1
-// only if they are needed.  Smaller systems always speculate: their fine stages leave most of
+// increments), or, at k = 2 where there is no trend yet, when eta~^1 is within kSpecFirst of
+// tol (measured ratios eta~^2 / eta~^1 run from 0.004 to 0.2, so such an iteration 2 may well
+// converge, and a wasted iteration costs far more than the overlap of one sweep): the host then
+// reads eta~^k first and enqueues the fine solves of iteration k+1 only if they are needed.  Smaller systems always speculate: their fine stages leave most of
 // the GPU idle, and a wrong prediction (e.g. increments that level off at the float32 floor of
 // the pair sum) would cost the overlap.  No kernel waits on another kernel.
 #include <chrono>
@@ -34,6 +36,7 @@ using namespace mrs;
 namespace {
 
 constexpr double kSpecPoints = 65536.0;   // points per batched fine stage that fill the GPU
+constexpr double kSpecFirst = 1e3;        // k = 2: speculate only if eta~^1 >= kSpecFirst tol
 
 struct DBuf {
     double* p = nullptr;
@@ -251,9 +254,13 @@ extern "C" int parareal_run_pipelined(mrs_ctx* ctx, int n_rods, const int64_t* r
         // The next sweep overwrites U[n] only after the group reading U[n] has copied it.
         fine_queued = false;
         bool speculate = k < max_iter && k < Ns;
-        if (speculate && tol > 0.0 && k >= 3 && (double)N1 * Ns >= kSpecPoints) {
-            const double a = stats.incr[k - 2], b = stats.incr[k - 3];   // eta~^{k-1}, eta~^{k-2}
-            if (b > 0.0 && a < b && a * (a / b) < tol) speculate = false;
+        if (speculate && tol > 0.0 && k >= 2 && (double)N1 * Ns >= kSpecPoints) {
+            if (k == 2) {
+                if (stats.incr[0] < kSpecFirst * tol) speculate = false;
+            } else {
+                const double a = stats.incr[k - 2], b = stats.incr[k - 3];   // eta~^{k-1}, eta~^{k-2}
+                if (b > 0.0 && a < b && a * (a / b) < tol) speculate = false;
+            }
         }
         if (speculate) {
             if ((st = enqueue_fine(k + 1))) return st;

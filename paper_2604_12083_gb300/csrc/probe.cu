@@ -1,0 +1,106 @@
+// probe.cu -- throughput of the FP32 FMA pipe (a measurement aid, not part of the method).
+//
+// The pair-sum kernels are bound by FP32 arithmetic on the CUDA cores; their roofline is the
+// FP32 peak 2 x 128 lanes x SMs x clock.  This kernel measures what the FMA pipe sustains on
+// the device for three instruction streams: scalar FFMA, packed FFMA2 (fma.rn.f32x2, two lanes
+// per instruction, the form the pair-sum kernels use) and the two interleaved one to one.
+// Every thread runs 8 independent dependency chains (enough to cover the pipe latency at 8
+// warps per scheduler), so the count is issue- and pipe-bound, not latency-bound.
+#include "mrs_internal.h"
+
+namespace mrs {
+namespace {
+
+constexpr int kProbeBlock = 256;
+constexpr int kProbeChains = 8;
+
+// a scalar FMA the compiler cannot pair into a packed one
+__device__ __forceinline__ float fma_scalar(float x, float a, float b)
+{
+    float y;
+    asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(x), "f"(a), "f"(b));
+    return y;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kProbeBlock) fma_probe_kernel(float* out, int iters, float a, float b)
+{
+    float2 x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c)
+        x[c] = make_float2(threadIdx.x * 1e-7f + c, blockIdx.x * 1e-7f - c);
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) {
+            if (KIND == 0) {          // scalar: two FFMA per chain and step
+                x[c].x = fma_scalar(x[c].x, a, b);
+                x[c].y = fma_scalar(x[c].y, a, b);
+            } else if (KIND == 1) {   // packed: one FFMA2 per chain and step
+                x[c] = __ffma2_rn(x[c], a2, b2);
+            } else {                  // alternating scalar pair and packed by chain
+                if (c & 1) {
+                    x[c] = __ffma2_rn(x[c], a2, b2);
+                } else {
+                    x[c].x = fma_scalar(x[c].x, a, b);
+                    x[c].y = fma_scalar(x[c].y, a, b);
+                }
+            }
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) s += x[c].x + x[c].y;
+    out[blockIdx.x * kProbeBlock + threadIdx.x] = s;
+}
+
+}  // namespace
+}  // namespace mrs
+
+using namespace mrs;
+
+extern "C" int mrs_fma_probe(int device, int kind, int iters, double* tflops, float* ms)
+{
+    clear_error();
+    MRS_REQUIRE(kind >= 0 && kind <= 2, "kind must be 0 (FFMA), 1 (FFMA2) or 2 (mixed)");
+    MRS_REQUIRE(iters >= 1 && iters <= (1 << 24), "iters must be in 1..2^24");
+    MRS_REQUIRE(tflops != nullptr, "tflops is NULL");
+    MRS_CHECK_CUDA(cudaSetDevice(device));
+    int sms = 0, per_sm = 0;
+    MRS_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    MRS_CHECK_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, device));
+    const int blocks = sms * (per_sm / kProbeBlock);
+    float* out = nullptr;
+    if (cudaMalloc((void**)&out, sizeof(float) * (size_t)blocks * kProbeBlock) != cudaSuccess) {
+        set_error("probe buffer allocation failed");
+        return MRS_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (!e) e = cudaEventCreate(&e1);
+    auto launch = [&](int it) {
+        if (kind == 0) fma_probe_kernel<0><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
+        else if (kind == 1) fma_probe_kernel<1><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
+        else fma_probe_kernel<2><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
+        return cudaGetLastError();
+    };
+    if (!e) e = launch(iters / 8 + 1);   // warm-up
+    float t = 0.f;
+    if (!e) e = cudaEventRecord(e0);
+    if (!e) e = launch(iters);
+    if (!e) e = cudaEventRecord(e1);
+    if (!e) e = cudaEventSynchronize(e1);
+    if (!e) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) {
+        set_error("probe failed: %s", cudaGetErrorString(e));
+        return MRS_ECUDA;
+    }
+    // every chain step is two FP32 lane FMAs (two flops each), in every kind
+    const double flops = 4.0 * kProbeChains * (double)iters * blocks * kProbeBlock;
+    *tflops = flops / (t * 1e-3) / 1e12;
+    if (ms) *ms = t;
+    return MRS_OK;
+}

@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "MRS_OK", 1: "MRS_EINVAL", 2: "MRS_ENOMEM", 3: "MRS_ECUDA", 4
 # Every symbol include/mrs_gb300.h declares (kept in sync by tests/test_abi.py).
 EXPORTS = [
     "mrs_last_error", "mrs_version", "mrs_ctx_create", "mrs_ctx_destroy", "mrs_ctx_num_sms",
-    "mrs_ctx_set_fused_steps", "mrs_ctx_set_sym_pass_bytes",
+    "mrs_ctx_set_fused_steps", "mrs_ctx_set_sym_pass_bytes", "mrs_fma_probe",
     "mrs_velocity", "mrs_plan_create", "mrs_plan_execute", "mrs_plan_destroy",
     "mrs_plan_config_count", "mrs_plan_config_symmetric", "mrs_plan_config_info", "mrs_plan_info",
     "mrs_plan_scratch",
@@ -113,6 +113,8 @@ def lib():
         L.mrs_ctx_num_sms.argtypes = [_vp]
         L.mrs_ctx_set_fused_steps.argtypes = [_vp, ctypes.c_int]
         L.mrs_ctx_set_sym_pass_bytes.argtypes = [_vp, ctypes.c_size_t]
+        L.mrs_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+                                    ctypes.POINTER(ctypes.c_float)]
         L.mrs_device_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint)]
         L.mrs_velocity.argtypes = [_vp, ctypes.c_int, _i64p, _vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _vp]
@@ -253,6 +255,14 @@ def mrs_reserve(ctx: Context, offsets, mu, eps, eps_per_sys=None, precision=MRS_
         peps = eps_arr.ctypes.data_as(_dp)
     _check(lib().mrs_reserve(ctx.handle, len(off) - 1, poff, float(mu), float(eps), peps,
                              int(precision)))
+
+
+def fma_probe(device, kind, iters=1 << 16):
+    """``mrs_fma_probe``: (TFLOP/s, ms) of the FP32 FMA pipe for kind 0 (FFMA), 1 (FFMA2),
+    2 (interleaved)."""
+    tf, ms = ctypes.c_double(), ctypes.c_float()
+    _check(lib().mrs_fma_probe(int(device), int(kind), int(iters), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def mrs_velocity_noalloc(n_points, X, f, n, u, w, mu, eps, stream=None):

@@ -599,3 +599,15 @@ def test_single_point_closed_form_and_zero_sources(ctx):
     for config in (None, 8, 25):
         u, w = run(ctx, z, mrs.MRS_F32_COMP, config=config)
         assert not u.any() and not w.any()
+
+
+def test_fma_probe_reports_pipe_throughput(ctx):
+    """mrs_fma_probe runs each instruction stream and reports a throughput between a tenth of
+    and slightly above the nominal FP32 peak (2 x 128 lanes x SMs x 2.07 GHz)."""
+    from paper_2604_12083_gb300 import mrs
+    nominal = 2 * 128 * ctx.num_sms * 2.07e9 / 1e12
+    for kind in (0, 1, 2):
+        tf, ms = mrs.fma_probe(0, kind, 1 << 14)
+        assert ms > 0 and 0.1 * nominal < tf < 1.1 * nominal, (kind, tf, nominal)
+    with pytest.raises(mrs.MrsError):
+        mrs.fma_probe(0, 3, 16)
