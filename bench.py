@@ -432,6 +432,54 @@ def extra_parareal(ctx, dev):
     return out
 
 
+def run_large_system(args):
+    """One system of 2^18 + 17 points (uniform in a 40^3 box, Gaussian f and n, eps = 0.02; the
+    large-system parity test's input): the symmetric pair sum in the library's default plan (its
+    column partials split into passes of at most 256 MiB) and in one pass, with the plan's
+    passes and scratch, timed with CUDA events (inputs far larger than L2 are not needed: the
+    kernel is ALU-bound; 92 flops per ordered pair against the FP32 peak)."""
+    import torch
+    from paper_2604_12083_gb300 import build as B, mrs, workloads as W
+    B.build()
+    ctx = mrs.Context(0)
+    rng = np.random.default_rng(68)
+    N = (1 << 18) + 17
+    X = rng.uniform(0.0, 40.0, (N, 3)).astype(np.float32)
+    f = rng.standard_normal((N, 3)).astype(np.float32)
+    n = rng.standard_normal((N, 3)).astype(np.float32)
+    off = np.array([0, N], np.int64)
+    Xd, fd, nd = (torch.from_numpy(a).cuda() for a in (X, f, n))
+    u, w = torch.empty_like(Xd), torch.empty_like(Xd)
+    peak, _ = fp32_peak_tflops(ctx.num_sms, load_peaks())
+    clk = ClockSampler(0)
+    clk.start()
+    out = {"case": "large_system", "workload": "one system of 2^18 + 17 points", "pairs": N * N,
+           "runs": []}
+    for pass_bytes, label in ((256 << 20, "default (passes of 256 MiB)"), (4 << 30, "one pass")):
+        ctx.set_sym_pass_bytes(pass_bytes)
+        pl = mrs.Plan(ctx, off, 1.0, 0.02, precision=mrs.MRS_F32_COMP, config=-1)
+        ctx.set_sym_pass_bytes(256 << 20)
+        pl.execute(Xd, fd, nd, u, w)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            pl.execute(Xd, fd, nd, u, w)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = min(ts)
+        tf = 92.0 * N * N / (ms * 1e-3) / 1e12
+        out["runs"].append({"plan": label, "config": pl.info()["config"], **pl.scratch(),
+                            "ms": ms, "tflops": tf, "frac_of_fp32_peak": tf / peak})
+        pl.close()
+    out["clocks"] = clk.stop()
+    out["peak_tflops"] = peak
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def run_fp32_peak(args):
     """The FP32 FMA pipe's throughput on this GPU (mrs_fma_probe): scalar FFMA, packed FFMA2 and
     the two interleaved, against the nominal 2 x 128 lanes x SMs x maximum SM clock, with the SM
@@ -1074,7 +1122,8 @@ def main():
     ap.add_argument("--config", type=int, default=-1,
                     help="force this pair-sum plan configuration (default: the library's choice)")
     ap.add_argument("--case", choices=["main", "rod_kernels", "parareal", "small_systems",
-                                       "paper_sizes", "batch", "serve", "parareal_horizon", "fp32_peak"],
+                                       "paper_sizes", "batch", "serve", "parareal_horizon", "fp32_peak",
+                                       "large_system"],
                     default="main",
                     help="rod_kernels: time the rod force and update kernels on 1M nodes; "
                          "parareal: the Parareal measurements alone; small_systems: latency of "
@@ -1114,6 +1163,9 @@ def main():
         return
     if args.case == "fp32_peak":
         run_fp32_peak(args)
+        return
+    if args.case == "large_system":
+        run_large_system(args)
         return
     if args.case == "serve":
         import torch

@@ -124,6 +124,8 @@ MRS_API int mrs_fma_probe(int device, int kind, int iters, double* tflops, float
  * (MRS_FLAG_NONFINITE: a non-finite u or omega was written, e.g. from non-finite inputs).
  * Synchronizes the device, returns the flags in *flags and clears them. */
 #define MRS_FLAG_NONFINITE 1u
+#define MRS_FLAG_BOUNDS    2u   /* debug build only: a work-table or node-table index was out of
+                                   range; the access was skipped (results are then invalid) */
 MRS_API int mrs_device_status(mrs_ctx* ctx, unsigned int* flags);
 
 /* ==========================================================================================

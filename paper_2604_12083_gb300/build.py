@@ -4,7 +4,9 @@ Each ``csrc/*.cu`` translation unit is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo``, then linked with ``-shared`` against
 the shared CUDA runtime (so that a process which already loaded libcudart -- e.g. through
 PyTorch -- uses a single runtime).  Rebuilds only when a source or header is newer than the
-library.
+library.  ``build(debug=True)`` builds ``_build/libmrs_gb300_debug.so`` with
+``-DMRS_DEBUG_BOUNDS=1``: every kernel checks the table entries it indexes through and raises
+MRS_FLAG_BOUNDS instead of touching memory through a bad one (loaded when MRS_GB300_DEBUG=1).
 """
 from __future__ import annotations
 
@@ -19,6 +21,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmrs_gb300.so")
+LIB_DEBUG = os.path.join(BUILD, "libmrs_gb300_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,28 +43,32 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not _stale(lib):
+        return lib
     nv = nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    objdir = os.path.join(BUILD, "debug") if debug else BUILD
+    os.makedirs(objdir, exist_ok=True)
     flags = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-fvisibility=hidden",
              "-I", os.path.join(ROOT, "include")] + ARCH
+    if debug:
+        flags += ["-DMRS_DEBUG_BOUNDS=1"]
     if verbose:
         flags += ["-Xptxas", "-v"]
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nv] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -73,17 +80,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
             objs.append(obj)
             if verbose and log:
                 print(log)
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     libdir = _cuda_lib_dir(nv)
     cmd = [nv, "-shared"] + ARCH + ["-cudart", "shared", "-o", tmp] + objs + \
         ["-Xlinker", "-rpath=" + libdir, "-L", libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -402,6 +402,7 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
         L.partial = p->d_partial;
         L.counters = p->d_counters;
         L.err = p->ctx->d_err;
+        L.n_points = p->n_points;
         if (p->sym_config >= 0 && (Xt == nullptr || Xt == X)) {
             SymLaunch S;
             S.tiles = p->d_stiles;
@@ -417,6 +418,16 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
             S.colpart = p->d_colpart;
             S.acc = p->d_acc;
             S.err = L.err;
+            S.n_points = p->n_points;
+            {
+                long long cu = 0, rs = 0;
+                for (const SymPass& ps : p->passes) {
+                    cu = std::max(cu, ps.W);
+                    rs = std::max(rs, ps.nseg);
+                }
+                S.col_units = cu;
+                S.row_segs = rs;
+            }
             e = cudaSuccess;
             for (const SymPass& ps : p->passes) {   // in order: each pass reuses the buffers
                 S.W = ps.W;

@@ -116,6 +116,7 @@ struct MrsLaunch {
     float* w;
     float* partial;       // [2P][6][TM] floats
     int* counters;        // [n_tiles], zero between launches
+    long long n_points;   // points of the arrays (index checks of the debug build)
     unsigned int* err;    // device error word: bit 0 = a non-finite output was written
 };
 
@@ -180,6 +181,9 @@ struct SymLaunch {
     long long U0;         // first work unit of this pass (global unit index; 0: one pass)
     int ta, tb, tc;       // tiles of this pass [ta, tb); the reduction covers tiles [ta, tc)
     float2* acc;          // [points][6] Kahan pairs carried between passes (NULL: one pass)
+    long long n_points;   // points of the arrays (index checks of the debug build)
+    long long col_units;  // work units the column-partial buffer holds
+    long long row_segs;   // row segments the row-partial buffer holds
     const SysConst* sc;
     const float* X;
     const float* f;

@@ -33,6 +33,7 @@
 // Float64 path (MRS_F64): one CTA per 128 targets, all sources of the system staged through
 // shared memory, float64 arithmetic with the kernels written in r^2.
 #include "mrs_device.cuh"
+#include "mrs_checks.h"
 #include "mrs_internal.h"
 
 namespace mrs {
@@ -201,7 +202,20 @@ mrs_f32_persistent(const MrsLaunch L)
     bool first_seg = true;
 
     while (ubeg < uend) {
+#if MRS_DEBUG_BOUNDS
+        // every thread of the CTA reads the same tile, so the CTA leaves together
+        if (ti < 0 || ti >= L.n_tiles) {
+            if (tid == 0) atomicOr(L.err, MRS_FLAG_BOUNDS);
+            return;
+        }
+#endif
         const TileDesc T = L.tiles[ti];
+#if MRS_DEBUG_BOUNDS
+        if (!ordered_tile_ok(T, TM, L.n_points) || ubeg < T.u0 || ubeg >= T.u0 + T.nu) {
+            if (tid == 0) atomicOr(L.err, MRS_FLAG_BOUNDS);
+            return;
+        }
+#endif
         const long long send = min(uend, T.u0 + (long long)T.nu);
         const int ua = (int)(ubeg - T.u0), ub = (int)(send - T.u0);
         const bool full = (ua == 0 && ub == T.nu);
@@ -379,6 +393,12 @@ mrs_f32_persistent(const MrsLaunch L)
                 // CTA order.
                 const int q_lo = cta_of_unit(L.W, L.P, T.u0);
                 const int q_hi = cta_of_unit(L.W, L.P, T.u0 + T.nu - 1);
+#if MRS_DEBUG_BOUNDS
+                if (q_lo < 0 || q_hi >= L.P || q_lo > q_hi) {   // contributor slots outside [0, 2P)
+                    if (tid == 0) atomicOr(L.err, MRS_FLAG_BOUNDS);
+                    return;
+                }
+#endif
                 const int sl_lo = 2 * q_lo + (unit_start(L.W, L.P, q_lo) < T.u0 ? 1 : 0);
                 constexpr int NB = 8;
 #pragma unroll 1

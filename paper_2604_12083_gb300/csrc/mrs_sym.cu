@@ -20,6 +20,7 @@
 // transposing shuffle reduction (8 shuffles for 6 values) and over the CTA's warps through
 // shared memory, then written to the column partial of its work unit.  The tile's points keep
 // their share in registers, folded per chunk into Kahan pairs in MRS_F32_COMP.
+#include "mrs_checks.h"
 #include "mrs_device.cuh"
 #include "mrs_internal.h"
 
@@ -194,7 +195,21 @@ mrs_f32_sym(const SymLaunch L)
     }
 
     while (ubeg < uend) {
+#if MRS_DEBUG_BOUNDS
+        // every thread of the CTA reads the same tile, so the CTA leaves together
+        if (ti < L.ta || ti >= L.tb) {
+            if (tid == 0) atomicOr(L.err, MRS_FLAG_BOUNDS);
+            return;
+        }
+#endif
         const SymTile T = L.tiles[ti];
+#if MRS_DEBUG_BOUNDS
+        if (!sym_tile_ok(T, TM, L.n_points, L.U0, L.col_units, L.row_segs) || ubeg < T.u0 ||
+            ubeg >= T.u0 + T.nu || p < T.qlo || p - T.qlo >= T.nseg) {
+            if (tid == 0) atomicOr(L.err, MRS_FLAG_BOUNDS);
+            return;
+        }
+#endif
         const long long seg_end = min(uend, T.u0 + (long long)T.nu);
         const int ua = (int)(ubeg - T.u0), ub = (int)(seg_end - T.u0);
         const SysConst sys = L.sc[T.sys];
@@ -407,10 +422,24 @@ __global__ void __launch_bounds__(256) mrs_sym_reduce(const SymLaunch L)
     const int q = (int)(pq - pt * 6);
     const int tl = (int)(pt / L.TM), li = (int)(pt - (long long)tl * L.TM);
     const int ti = L.ta + tl;
+#if MRS_DEBUG_BOUNDS
+    if (ti >= L.n_tiles) {
+        atomicOr(L.err, MRS_FLAG_BOUNDS);
+        return;
+    }
+#endif
     const SymTile T = L.tiles[ti];
     if (li >= T.tn) return;   // the whole lane group leaves together
     const int j = T.t0 + li;
     const bool own = ti < L.tb;
+#if MRS_DEBUG_BOUNDS
+    // the units of a later tile lie in a later pass: only its extent is checked
+    if (!sym_tile_ok(T, L.TM, L.n_points, own ? L.U0 : T.u0, own ? L.col_units : T.nu, L.row_segs) ||
+        T.tfirst > ti) {
+        if (r == 0) atomicOr(L.err, MRS_FLAG_BOUNDS);
+        return;   // the whole lane group reads the same tile and leaves together
+    }
+#endif
     float sum = 0.f, cmp = 0.f;
     if (r == 0 && T.tfirst < L.ta) {   // an earlier pass holds tiles of this system
         const float2 a = L.acc[(long long)j * 6 + q];
@@ -430,6 +459,13 @@ __global__ void __launch_bounds__(256) mrs_sym_reduce(const SymLaunch L)
                 v[a] = __ldcg(L.rowpart + ((long long)(T.seg0 + k) * L.TM + li) * 6 + q);
             } else if (k < nterm) {
                 const SymTile& R = L.tiles[c0 + (k - nrow)];
+#if MRS_DEBUG_BOUNDS
+                if (!sym_tile_ok(R, L.TM, L.n_points, L.U0, L.col_units, L.row_segs) || j < R.t0 ||
+                    j >= R.send) {
+                    atomicOr(L.err, MRS_FLAG_BOUNDS);
+                    continue;   // the term is skipped
+                }
+#endif
                 v[a] = __ldcg(L.colpart + ((R.u0 - L.U0) * kUnitSources + (j - R.t0)) * 6 + q);
             }
         }

@@ -180,6 +180,7 @@ extern "C" int mrs_velocity_noalloc(int64_t n_points, const float* X, const floa
     L.w = w;
     L.partial = partial;
     L.counters = counters;
+    L.n_points = N;
     // the kernel's non-finite-input flag goes to a word of the array that is never read back:
     // this entry point does not report non-finite inputs (the outputs carry the NaN/Inf)
     L.err = (unsigned int*)(base + kNaOffErr);

@@ -174,6 +174,7 @@ RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt)
     L.inv_L = 1.0 / p->L;
     set_pack_reference(L, ws->n_rods, ws->rod_off.data());
     L.segsc = (ws->segsc_k == p->wave_k && ws->segsc_L == p->L) ? ws->d_segsc : nullptr;
+    L.err = ws->ctx ? ws->ctx->d_err : nullptr;
     return L;
 }
 

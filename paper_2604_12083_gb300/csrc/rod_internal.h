@@ -26,6 +26,7 @@ struct RodLaunch {
     // [N] (sin, cos) of k_w s_mid for the segment k+1/2 of every node (Omega_2 by angle
     // addition, one sincos(f t) per CTA), or NULL: sin(k_w s_mid + f t) per segment
     const double2* segsc;
+    unsigned int* err;         // device error word (MRS_FLAG_BOUNDS of the debug build), or NULL
 };
 
 // The reference nodes of an instance with rods rod_off[0..n_rods]: the middle node of up to 8
@@ -70,6 +71,7 @@ cudaError_t launch_rod_fine_fused(const RodLaunch& L, double* X, double* D, int 
                                   double mu, double eps, cudaStream_t s);
 cudaError_t launch_set_times(double* t0, int n_inst, double t_first, double dT, long long* step,
                              cudaStream_t s);
+
 
 // One batch of n_inst identical rod sets (instance i = the rods of rod_off shifted by i*N1
 // nodes); every instance is its own hydrodynamic system.

@@ -16,9 +16,23 @@
 // paper, reached without trigonometric calls or endpoint branches.
 #include <cmath>
 
+#include "mrs_checks.h"
 #include "rod_internal.h"
 
 namespace mrs {
+
+// Debug build: a node table entry outside its rod raises MRS_FLAG_BOUNDS and the node is
+// skipped (returns false).
+__device__ __forceinline__ bool node_checked(const RodLaunch& L, int2 ni, long long k, long long N)
+{
+#if MRS_DEBUG_BOUNDS
+    if (!rod_node_ok(ni, k, N)) {
+        if (L.err) atomicOr(L.err, MRS_FLAG_BOUNDS);
+        return false;
+    }
+#endif
+    return true;
+}
 
 __device__ __forceinline__ double dot3(const double* a, const double* b)
 {
@@ -182,6 +196,7 @@ __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.N) return;
     const int2 ni = L.node_info[k];
+    if (!node_checked(L, ni, k, L.N)) return;
     if (ni.x >= ni.y - 1) return;  // last node of its rod: no segment
     segment_fn(L, X, D, t_off, k, ni.x, ni.y, L.FN + 6 * (size_t)k);
 }
@@ -257,6 +272,7 @@ __global__ void rod_node_kernel(const RodLaunch L, const double* __restrict__ X,
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.N) return;
     const int2 ni = L.node_info[k];
+    if (!node_checked(L, ni, k, L.N)) return;
     double ref[3];
     const bool centred = Xf && L.n_ref > 0;
     if (centred) pack_reference(L, X + 3 * (size_t)(k / L.nodes_per_inst) * L.nodes_per_inst, ref);
@@ -278,7 +294,14 @@ __global__ void __launch_bounds__(kRodChunk) rod_forces_fused_kernel(
     __shared__ double sref[3];
     __shared__ double ssc[2];   // sin(f t), cos(f t) of the chunk's instance
     const long long k0 = L.chunks[blockIdx.x];
+#if MRS_DEBUG_BOUNDS
+    if (k0 < 0 || k0 >= L.N) {   // every thread reads the same chunk: the CTA leaves together
+        if (threadIdx.x == 0 && L.err) atomicOr(L.err, MRS_FLAG_BOUNDS);
+        return;
+    }
+#endif
     const int2 ni0 = L.node_info[k0];
+    if (!node_checked(L, ni0, k0, L.N)) return;   // the same entry for every thread of the CTA
     const int M = ni0.y, t = threadIdx.x;
     const int s = ni0.x - 1 + t;   // segment index within the rod
     const int inst = (int)(k0 / L.nodes_per_inst);   // a chunk lies in one rod, hence in one instance
@@ -587,7 +610,8 @@ __global__ void __launch_bounds__(BLOCK) rod_fine_fused_kernel(const RodLaunch L
     for (int q = threadIdx.x; q < 3 * N1; q += BLOCK) sX[q] = gX[q];
     for (int q = threadIdx.x; q < 9 * N1; q += BLOCK) sD[q] = gD[q];
     for (int k = threadIdx.x; k < N1; k += BLOCK) {
-        const int2 ni = L.node_info[k];
+        int2 ni = L.node_info[k];
+        if (!node_checked(L, ni, k, N1)) ni = make_int2(0, 1);   // skipped: a node with no segment
         sni[k] = ni;
         const double ds = L.p.L / (double)(ni.y - 1);
         double sk, ck;

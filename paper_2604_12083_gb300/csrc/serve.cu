@@ -314,6 +314,7 @@ cudaError_t admit_enqueue(mrs_server* S, SJob* j)
     L.inv_L = 1.0 / J.params.L;
     set_pack_reference(L, J.n_rods, j->rod_off.data());
     L.segsc = nullptr;    // two-kernel force path: sin(k_w s_mid + f t) per segment
+    L.err = S->ctx->d_err;
     return cudaSuccess;
 }
 
@@ -435,6 +436,9 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
         L.tb = snt;
         L.tc = snt;
         L.acc = nullptr;
+        L.n_points = (long long)S->pts.capacity();
+        L.col_units = (long long)(S->colpart_cap / (kUnitSources * 6));
+        L.row_segs = (long long)(S->rowpart_cap / ((size_t)S->sTM * 6));
         L.sc = S->d_sc;
         L.X = S->pX;
         L.f = S->pf;
@@ -461,6 +465,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
         L.partial = S->d_partial;
         L.counters = S->d_counters;
         L.err = S->ctx->d_err;
+        L.n_points = (long long)S->pts.capacity();
         if ((e = launch_mrs_f32(S->config, true, L, s))) return e;
     }
     // stage updates and copy-out

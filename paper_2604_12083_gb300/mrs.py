@@ -15,7 +15,10 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libmrs_gb300.so")
+# MRS_GB300_DEBUG=1 loads the debug build (index checks that raise MRS_FLAG_BOUNDS instead of
+# touching memory through a bad table entry; paper_2604_12083_gb300.build.build(debug=True))
+LIB_PATH = os.path.join(HERE, "_build", "libmrs_gb300_debug.so" if os.environ.get("MRS_GB300_DEBUG") == "1"
+                        else "libmrs_gb300.so")
 
 MRS_OK, MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA, MRS_ETIMEOUT, MRS_ENOCONV, MRS_EBUSY, MRS_PENDING = range(8)
 MRS_ECANCELED = 8
@@ -39,7 +42,7 @@ EXPORTS = [
     "rod_advance", "rod_checkpoint_save", "rod_checkpoint_load", "mrs_device_status",
     "mrs_reserve",
 ]
-MRS_FLAG_NONFINITE = 1
+MRS_FLAG_NONFINITE, MRS_FLAG_BOUNDS = 1, 2
 MRS_JOB_VELOCITY, MRS_JOB_ROD = 0, 1
 
 _vp = ctypes.c_void_p
