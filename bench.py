@@ -491,18 +491,19 @@ def run_fp32_peak(args):
     clk = ClockSampler(0)
     clk.start()
     res = {}
-    for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "ffma_ffma2_interleaved")):
+    for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "ffma_ffma2_interleaved"), (3, "dfma_fp64")):
         best = None
         for _ in range(5):
-            tf, ms = mrs.fma_probe(0, kind, 1 << 18)
+            tf, ms = mrs.fma_probe(0, kind, (1 << 18) if kind < 3 else (1 << 13))
             if best is None or tf > best[0]:
                 best = (tf, ms)
         res[name] = {"tflops": best[0], "ms": best[1]}
     clocks = clk.stop()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak = 2 * 128 * sms * float(load_peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    for v in res.values():
-        v["frac_of_nominal"] = v["tflops"] / peak
+    for k, v in res.items():
+        if not k.startswith("dfma"):
+            v["frac_of_nominal"] = v["tflops"] / peak
     print(json.dumps({"case": "fp32_peak", "nominal_tflops": peak, "sms": sms,
                       "nominal_basis": "2 x 128 FP32 lanes x SMs x max SM clock", **res,
                       "clocks": clocks}), flush=True)

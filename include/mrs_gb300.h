@@ -113,8 +113,9 @@ MRS_API int mrs_ctx_set_sym_pass_bytes(mrs_ctx* ctx, size_t bytes);
 
 /* Measurement aid (the paper has no counterpart): FP32 FMA-pipe throughput of the device, in
  * TFLOP/s (2 flops per lane FMA), for kind 0: scalar FFMA, 1: packed FFMA2 (fma.rn.f32x2, the
- * form the pair-sum kernels use), 2: the two interleaved.  One launch of every resident
- * thread running 8 independent chains of `iters` steps (two lane FMAs per chain and step),
+ * form the pair-sum kernels use), 2: the two interleaved, 3: float64 DFMA (the pipe the rod
+ * kernels are bound by).  One launch of every resident thread running 8 independent chains of
+ * `iters` steps (two FP32 lane FMAs, or one DFMA, per chain and step),
  * timed with CUDA events after a warm-up launch; *ms (may be NULL) gets the launch's time.
  * Allocates and frees a small buffer and synchronizes the device.
  * Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */

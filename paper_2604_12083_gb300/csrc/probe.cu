@@ -1,9 +1,11 @@
-// probe.cu -- throughput of the FP32 FMA pipe (a measurement aid, not part of the method).
+// probe.cu -- throughput of the FP32 FMA pipe and of the FP64 pipe (a measurement aid, not part
+// of the method).
 //
 // The pair-sum kernels are bound by FP32 arithmetic on the CUDA cores; their roofline is the
 // FP32 peak 2 x 128 lanes x SMs x clock.  This kernel measures what the FMA pipe sustains on
 // the device for three instruction streams: scalar FFMA, packed FFMA2 (fma.rn.f32x2, two lanes
-// per instruction, the form the pair-sum kernels use) and the two interleaved one to one.
+// per instruction, the form the pair-sum kernels use) and the two interleaved one to one; and
+// what the float64 pipe sustains for DFMA (the rod kernels are bound by it).
 // Every thread runs 8 independent dependency chains (enough to cover the pipe latency at 8
 // warps per scheduler), so the count is issue- and pipe-bound, not latency-bound.
 #include "mrs_internal.h"
@@ -20,6 +22,22 @@ __device__ __forceinline__ float fma_scalar(float x, float a, float b)
     float y;
     asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(x), "f"(a), "f"(b));
     return y;
+}
+
+// float64: 8 independent DFMA chains per thread
+__global__ void __launch_bounds__(kProbeBlock) dfma_probe_kernel(float* out, int iters, double a, double b)
+{
+    double x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) x[c] = threadIdx.x * 1e-9 + blockIdx.x * 1e-7 + c;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) s += x[c];
+    out[blockIdx.x * kProbeBlock + threadIdx.x] = (float)s;
 }
 
 template <int KIND>
@@ -62,7 +80,7 @@ using namespace mrs;
 extern "C" int mrs_fma_probe(int device, int kind, int iters, double* tflops, float* ms)
 {
     clear_error();
-    MRS_REQUIRE(kind >= 0 && kind <= 2, "kind must be 0 (FFMA), 1 (FFMA2) or 2 (mixed)");
+    MRS_REQUIRE(kind >= 0 && kind <= 3, "kind must be 0 (FFMA), 1 (FFMA2), 2 (mixed) or 3 (DFMA)");
     MRS_REQUIRE(iters >= 1 && iters <= (1 << 24), "iters must be in 1..2^24");
     MRS_REQUIRE(tflops != nullptr, "tflops is NULL");
     MRS_CHECK_CUDA(cudaSetDevice(device));
@@ -81,7 +99,8 @@ extern "C" int mrs_fma_probe(int device, int kind, int iters, double* tflops, fl
     auto launch = [&](int it) {
         if (kind == 0) fma_probe_kernel<0><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
         else if (kind == 1) fma_probe_kernel<1><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
-        else fma_probe_kernel<2><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
+        else if (kind == 2) fma_probe_kernel<2><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
+        else dfma_probe_kernel<<<blocks, kProbeBlock>>>(out, it, 0.999, 1e-3);
         return cudaGetLastError();
     };
     if (!e) e = launch(iters / 8 + 1);   // warm-up
@@ -98,8 +117,8 @@ extern "C" int mrs_fma_probe(int device, int kind, int iters, double* tflops, fl
         set_error("probe failed: %s", cudaGetErrorString(e));
         return MRS_ECUDA;
     }
-    // every chain step is two FP32 lane FMAs (two flops each), in every kind
-    const double flops = 4.0 * kProbeChains * (double)iters * blocks * kProbeBlock;
+    // every chain step is two FP32 lane FMAs (two flops each) in kinds 0..2, one DFMA in kind 3
+    const double flops = (kind == 3 ? 2.0 : 4.0) * kProbeChains * (double)iters * blocks * kProbeBlock;
     *tflops = flops / (t * 1e-3) / 1e12;
     if (ms) *ms = t;
     return MRS_OK;

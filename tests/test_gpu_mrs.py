@@ -609,5 +609,7 @@ def test_fma_probe_reports_pipe_throughput(ctx):
     for kind in (0, 1, 2):
         tf, ms = mrs.fma_probe(0, kind, 1 << 14)
         assert ms > 0 and 0.1 * nominal < tf < 1.1 * nominal, (kind, tf, nominal)
+    tf, ms = mrs.fma_probe(0, 3, 1 << 10)        # float64: a small fraction of the FP32 rate
+    assert ms > 0 and 0.0 < tf < 0.2 * nominal, tf
     with pytest.raises(mrs.MrsError):
-        mrs.fma_probe(0, 3, 16)
+        mrs.fma_probe(0, 4, 16)
