@@ -498,6 +498,12 @@ def run_fp32_peak(args):
             if best is None or tf > best[0]:
                 best = (tf, ms)
         res[name] = {"tflops": best[0], "ms": best[1]}
+    for w in (1, 2, 4):   # the pair-sum kernel runs 2 warps per scheduler
+        best = None
+        for _ in range(3):
+            tf, ms = mrs.fma_probe(0, 1, 1 << 16, w)
+            best = tf if best is None or tf > best else best
+        res["ffma2_%d_warps_per_scheduler" % w] = {"tflops": best}
     clocks = clk.stop()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak = 2 * 128 * sms * float(load_peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 1e12

@@ -114,12 +114,14 @@ MRS_API int mrs_ctx_set_sym_pass_bytes(mrs_ctx* ctx, size_t bytes);
 /* Measurement aid (the paper has no counterpart): FP32 FMA-pipe throughput of the device, in
  * TFLOP/s (2 flops per lane FMA), for kind 0: scalar FFMA, 1: packed FFMA2 (fma.rn.f32x2, the
  * form the pair-sum kernels use), 2: the two interleaved, 3: float64 DFMA (the pipe the rod
- * kernels are bound by).  One launch of every resident thread running 8 independent chains of
- * `iters` steps (two FP32 lane FMAs, or one DFMA, per chain and step),
- * timed with CUDA events after a warm-up launch; *ms (may be NULL) gets the launch's time.
- * Allocates and frees a small buffer and synchronizes the device.
+ * kernels are bound by).  One launch in which every thread runs 8 independent chains of `iters`
+ * steps (two FP32 lane FMAs, or one DFMA, per chain and step): warps_per_scheduler = 0 fills
+ * every thread slot of the device; w >= 1 runs w warps on each scheduler of each SM (the
+ * pair-sum kernel runs 2).  Timed with CUDA events after a warm-up launch; *ms (may be NULL)
+ * gets the launch's time.  Allocates and frees a small buffer and synchronizes the device.
  * Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */
-MRS_API int mrs_fma_probe(int device, int kind, int iters, double* tflops, float* ms);
+MRS_API int mrs_fma_probe(int device, int kind, int iters, int warps_per_scheduler,
+                          double* tflops, float* ms);
 
 /* Device-side anomaly flags raised by the pair-sum kernels of this context since the last call
  * (MRS_FLAG_NONFINITE: a non-finite u or omega was written, e.g. from non-finite inputs).

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kProbeBlock) dfma_probe_kernel(float* out, int
     double s = 0.0;
 #pragma unroll
     for (int c = 0; c < kProbeChains; ++c) s += x[c];
-    out[blockIdx.x * kProbeBlock + threadIdx.x] = (float)s;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
 }
 
 template <int KIND>
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kProbeBlock) fma_probe_kernel(float* out, int 
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < kProbeChains; ++c) s += x[c].x + x[c].y;
-    out[blockIdx.x * kProbeBlock + threadIdx.x] = s;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 }  // namespace
@@ -77,19 +77,25 @@ __global__ void __launch_bounds__(kProbeBlock) fma_probe_kernel(float* out, int 
 
 using namespace mrs;
 
-extern "C" int mrs_fma_probe(int device, int kind, int iters, double* tflops, float* ms)
+extern "C" int mrs_fma_probe(int device, int kind, int iters, int warps_per_scheduler,
+                             double* tflops, float* ms)
 {
     clear_error();
     MRS_REQUIRE(kind >= 0 && kind <= 3, "kind must be 0 (FFMA), 1 (FFMA2), 2 (mixed) or 3 (DFMA)");
     MRS_REQUIRE(iters >= 1 && iters <= (1 << 24), "iters must be in 1..2^24");
+    MRS_REQUIRE(warps_per_scheduler >= 0 && warps_per_scheduler <= 16,
+                "warps_per_scheduler must be in 0..16");
     MRS_REQUIRE(tflops != nullptr, "tflops is NULL");
     MRS_CHECK_CUDA(cudaSetDevice(device));
     int sms = 0, per_sm = 0;
     MRS_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     MRS_CHECK_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, device));
-    const int blocks = sms * (per_sm / kProbeBlock);
+    // 0: every thread slot of every SM (CTAs of kProbeBlock); w >= 1: w CTAs of 128 threads per
+    // SM, i.e. w warps on each of the SM's four schedulers
+    const int threads = warps_per_scheduler ? 128 : kProbeBlock;
+    const int blocks = warps_per_scheduler ? sms * warps_per_scheduler : sms * (per_sm / kProbeBlock);
     float* out = nullptr;
-    if (cudaMalloc((void**)&out, sizeof(float) * (size_t)blocks * kProbeBlock) != cudaSuccess) {
+    if (cudaMalloc((void**)&out, sizeof(float) * (size_t)blocks * threads) != cudaSuccess) {
         set_error("probe buffer allocation failed");
         return MRS_ENOMEM;
     }
@@ -97,10 +103,10 @@ extern "C" int mrs_fma_probe(int device, int kind, int iters, double* tflops, fl
     cudaError_t e = cudaEventCreate(&e0);
     if (!e) e = cudaEventCreate(&e1);
     auto launch = [&](int it) {
-        if (kind == 0) fma_probe_kernel<0><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
-        else if (kind == 1) fma_probe_kernel<1><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
-        else if (kind == 2) fma_probe_kernel<2><<<blocks, kProbeBlock>>>(out, it, 0.999f, 1e-3f);
-        else dfma_probe_kernel<<<blocks, kProbeBlock>>>(out, it, 0.999, 1e-3);
+        if (kind == 0) fma_probe_kernel<0><<<blocks, threads>>>(out, it, 0.999f, 1e-3f);
+        else if (kind == 1) fma_probe_kernel<1><<<blocks, threads>>>(out, it, 0.999f, 1e-3f);
+        else if (kind == 2) fma_probe_kernel<2><<<blocks, threads>>>(out, it, 0.999f, 1e-3f);
+        else dfma_probe_kernel<<<blocks, threads>>>(out, it, 0.999, 1e-3);
         return cudaGetLastError();
     };
     if (!e) e = launch(iters / 8 + 1);   // warm-up
@@ -118,7 +124,7 @@ extern "C" int mrs_fma_probe(int device, int kind, int iters, double* tflops, fl
         return MRS_ECUDA;
     }
     // every chain step is two FP32 lane FMAs (two flops each) in kinds 0..2, one DFMA in kind 3
-    const double flops = (kind == 3 ? 2.0 : 4.0) * kProbeChains * (double)iters * blocks * kProbeBlock;
+    const double flops = (kind == 3 ? 2.0 : 4.0) * kProbeChains * (double)iters * blocks * threads;
     *tflops = flops / (t * 1e-3) / 1e12;
     if (ms) *ms = t;
     return MRS_OK;

@@ -116,7 +116,7 @@ def lib():
         L.mrs_ctx_num_sms.argtypes = [_vp]
         L.mrs_ctx_set_fused_steps.argtypes = [_vp, ctypes.c_int]
         L.mrs_ctx_set_sym_pass_bytes.argtypes = [_vp, ctypes.c_size_t]
-        L.mrs_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+        L.mrs_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
                                     ctypes.POINTER(ctypes.c_float)]
         L.mrs_device_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint)]
         L.mrs_velocity.argtypes = [_vp, ctypes.c_int, _i64p, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -260,11 +260,12 @@ def mrs_reserve(ctx: Context, offsets, mu, eps, eps_per_sys=None, precision=MRS_
                              int(precision)))
 
 
-def fma_probe(device, kind, iters=1 << 16):
+def fma_probe(device, kind, iters=1 << 16, warps_per_scheduler=0):
     """``mrs_fma_probe``: (TFLOP/s, ms) of the FP32 FMA pipe for kind 0 (FFMA), 1 (FFMA2),
-    2 (interleaved)."""
+    2 (interleaved), or of the FP64 pipe (kind 3); warps_per_scheduler 0 fills the device."""
     tf, ms = ctypes.c_double(), ctypes.c_float()
-    _check(lib().mrs_fma_probe(int(device), int(kind), int(iters), ctypes.byref(tf), ctypes.byref(ms)))
+    _check(lib().mrs_fma_probe(int(device), int(kind), int(iters), int(warps_per_scheduler),
+                               ctypes.byref(tf), ctypes.byref(ms)))
     return tf.value, ms.value
 
 
