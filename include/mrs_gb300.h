@@ -103,9 +103,9 @@ MRS_API int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable);
  * partials -- 24 bytes per source slot of every work unit, about N^2 / (2 TM) * 24 bytes for one
  * system of N points -- exceed it runs as several passes of about equal work over consecutive
  * tiles, each one launch of the pair kernel and one of the reduction kernel, reusing one buffer
- * (plus 48 bytes per point to carry sums between passes).  Default 256 MiB: the 32768-point
- * system (34 MB) runs in one pass, a 2^18-point one (2.1 GB) in 9, the 512-system batch of
- * 256..16384-point systems (515 MB) in 2.  Each further pass costs about 60 us on a GB300 (the
+ * (plus 48 bytes per point to carry sums between passes).  Default 192 MiB: the 32768-point
+ * system (34 MB) runs in one pass, a 2^18-point one (2.1 GB) in 11 with under 256 MB of
+ * scratch in all, the 512-system batch of 256..16384-point systems (515 MB) in 3.  Each further pass costs about 60 us on a GB300 (the
  * tail of one more persistent launch and one more reduction).  A pass holds at least one tile
  * row, so its buffer may exceed the setting by up to one row (N / 32 units).  Host only.
  * Errors: MRS_EINVAL (fewer bytes than one work unit's partials, 768). */

@@ -302,7 +302,7 @@ struct mrs_ctx {
     int fused_steps = 1;
     // largest column-partial buffer (bytes) of one pass of a symmetric plan; a plan with more
     // column partials is split into passes (mrs_ctx_set_sym_pass_bytes)
-    size_t sym_pass_bytes = (size_t)256 << 20;
+    size_t sym_pass_bytes = (size_t)192 << 20;
 };
 
 namespace mrs {

@@ -32,7 +32,7 @@ p = ragged_batch()
 ur, wr = oracle.mrs_velocity_batch(p.offsets, p.X, p.f, p.n, 0.0, p.mu, eps_per_sys=p.eps)
 X, f, n = (torch.from_numpy(a).cuda() for a in (p.X, p.f, p.n))
 nz = [s for s in range(len(p.offsets) - 1) if p.offsets[s] < p.offsets[s + 1]]
-for pass_bytes in (256 << 20, 3 * 768):
+for pass_bytes in (192 << 20, 3 * 768):
     ctx.set_sym_pass_bytes(pass_bytes)
     configs = range(mrs.plan_config_count()) if pass_bytes > 4096 else range(17, mrs.plan_config_count())
     for cfg in configs:
@@ -45,7 +45,7 @@ for pass_bytes in (256 << 20, 3 * 768):
         for s in nz:
             a, b = p.offsets[s], p.offsets[s + 1]
             worst = max(worst, rel(uu[a:b], ur[a:b]), rel(ww[a:b], wr[a:b]))
-ctx.set_sym_pass_bytes(256 << 20)
+ctx.set_sym_pass_bytes(192 << 20)
 # rod stepping: fused and graph paths against the oracle
 rs = W.rod_system(95, 3, 40, box=2.0)
 cfg = dict(W.ROD_PLAIN, a=(2e-3,) * 3, b=(20.0,) * 3)
