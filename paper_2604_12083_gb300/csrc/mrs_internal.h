@@ -15,6 +15,40 @@
 namespace mrs {
 
 // ---------------------------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of a time step (forces -> pair sum -> update) and
+// of a symmetric pair sum (pair kernel -> reduction) are launched with programmatic stream
+// serialization: a kernel may be scheduled while its predecessor's last CTAs are still running,
+// and waits (pdl_wait, griddepcontrol.wait) before its first access to memory, until the
+// predecessor has completed and its writes are visible.  This hides the launch gap between
+// dependent kernels (inside captured graphs too).  For a kernel launched without the attribute
+// the wait returns at once.  Every kernel launched through launch_pdl calls pdl_wait first, so
+// a kernel also never overwrites what its predecessor still reads.
+// ---------------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+#endif
+
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Errors: a per-thread message plus the int status of the C ABI.
 // ---------------------------------------------------------------------------------------------
 void set_error(const char* fmt, ...);

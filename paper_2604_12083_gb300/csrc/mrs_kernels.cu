@@ -170,6 +170,7 @@ template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL, bool SQ = fals
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, TPT>::value))
 mrs_f32_persistent(const MrsLaunch L)
 {
+    pdl_wait();
     constexpr int TM = BLOCK * TPT;
     __shared__ __align__(16) float sflat[kChunk * 12];
     __shared__ float2 kah[COMP ? 6 * TPT * BLOCK : 1];
@@ -463,8 +464,8 @@ const int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL, bool SQ>
 static cudaError_t launch_t(const MrsLaunch& L, cudaStream_t s)
 {
-    mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED, UNROLL, SQ><<<L.P, BLOCK, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_pdl(mrs_f32_persistent<BLOCK, TPT, COMP, PAIRED, UNROLL, SQ>, dim3(L.P), dim3(BLOCK), 0,
+                      s, L);
 }
 
 template <int BLOCK, int TPT, bool COMP, bool PAIRED, int UNROLL, bool SQ>
@@ -519,6 +520,7 @@ int occupancy_f32(int config, bool comp, int* ctas_per_sm)
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kF64Block) mrs_f64_kernel(const MrsLaunch64 L)
 {
+    pdl_wait();
     __shared__ double sx[kF64Block * 9];
     const int b = blockIdx.x;
     const int sys = L.tile_sys[b];
@@ -577,7 +579,8 @@ __global__ void __launch_bounds__(kF64Block) mrs_f64_kernel(const MrsLaunch64 L)
 cudaError_t launch_mrs_f64(const MrsLaunch64& L, cudaStream_t s)
 {
     if (L.n_blocks == 0) return cudaSuccess;
-    mrs_f64_kernel<<<L.n_blocks, kF64Block, 0, s>>>(L);
+    cudaError_t e = launch_pdl(mrs_f64_kernel, dim3(L.n_blocks), dim3(kF64Block), 0, s, L);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

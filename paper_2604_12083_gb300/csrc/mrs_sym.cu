@@ -165,6 +165,7 @@ template <int BLOCK, int TPT, bool COMP, bool SQ, bool SKEW, int UNR = 2, int MI
 __global__ void __launch_bounds__(BLOCK, (MINB ? MINB : SymMinBlocks<BLOCK, TPT>::value))
 mrs_f32_sym(const SymLaunch L)
 {
+    pdl_wait();
     static_assert(TPT % 2 == 0, "points are held in packs of two");
     constexpr int NP = TPT / 2;
     constexpr int TM = BLOCK * TPT;
@@ -414,6 +415,7 @@ constexpr int kRedSplit = 4;
 
 __global__ void __launch_bounds__(256) mrs_sym_reduce(const SymLaunch L)
 {
+    pdl_wait();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)(L.tc - L.ta) * L.TM * 6 * kRedSplit) return;   // whole lane groups
     const int r = (int)(idx % kRedSplit);
@@ -516,14 +518,12 @@ static cudaError_t sym_prepare()
 template <int BLOCK, int TPT, bool COMP, bool SQ, bool SKEW, int UNR, int MINB>
 static cudaError_t launch_sym_t(const SymLaunch& L, cudaStream_t s)
 {
-    mrs_f32_sym<BLOCK, TPT, COMP, SQ, SKEW, UNR, MINB>
-        <<<L.P, BLOCK, sym_smem_bytes<BLOCK, TPT, COMP>(), s>>>(L);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(mrs_f32_sym<BLOCK, TPT, COMP, SQ, SKEW, UNR, MINB>, dim3(L.P), dim3(BLOCK),
+                               sym_smem_bytes<BLOCK, TPT, COMP>(), s, L);
     if (e != cudaSuccess) return e;
     const long long n = (long long)(L.tc - L.ta) * L.TM * 6 * kRedSplit;
     if (n == 0) return cudaSuccess;
-    mrs_sym_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_pdl(mrs_sym_reduce, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, L);
 }
 
 template <int BLOCK, int TPT, bool COMP, bool SQ, bool SKEW, int UNR, int MINB>

@@ -193,6 +193,7 @@ __global__ void rod_segsc_kernel(int N, const int2* __restrict__ node_info, doub
 __global__ void rod_segment_kernel(const RodLaunch L, const double* __restrict__ X,
                                    const double* __restrict__ D, double t_off)
 {
+    pdl_wait();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.N) return;
     const int2 ni = L.node_info[k];
@@ -269,6 +270,7 @@ __device__ __forceinline__ void pack_reference(const RodLaunch& L, const double*
 __global__ void rod_node_kernel(const RodLaunch L, const double* __restrict__ X, double* g64,
                                 double* m64, float* Xf, float* gf, float* mf)
 {
+    pdl_wait();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.N) return;
     const int2 ni = L.node_info[k];
@@ -290,6 +292,7 @@ __global__ void __launch_bounds__(kRodChunk) rod_forces_fused_kernel(
     const RodLaunch L, const double* __restrict__ X, const double* __restrict__ D, double t_off,
     double* g64, double* m64, float* Xf, float* gf, float* mf)
 {
+    pdl_wait();
     __shared__ double sFN[kRodChunk * 6];
     __shared__ double sref[3];
     __shared__ double ssc[2];   // sin(f t), cos(f t) of the chunk's instance
@@ -370,6 +373,7 @@ __global__ void rod_update_kernel(const RodLaunch L, const double* X0, const dou
                                   const VT* __restrict__ u, const VT* __restrict__ w,
                                   double h, double* X1, double* D1, int bump_step)
 {
+    pdl_wait();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (bump_step && k == 0) *L.step += 1;
     if (k >= L.N) return;
@@ -705,6 +709,7 @@ constexpr int kLJTile = 256;
 
 __global__ void rod_lj_kernel(const RodLaunch L, const double* __restrict__ X, double* g64, float* gf)
 {
+    pdl_wait();
     __shared__ float sx[kLJTile * 3];
     __shared__ int skey[kLJTile];
     const int inst = blockIdx.y;
@@ -775,16 +780,20 @@ cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double*
 {
     if (L.N == 0) return cudaSuccess;
     if (L.chunks != nullptr) {
-        rod_forces_fused_kernel<<<L.n_chunks, kRodChunk, 0, s>>>(L, X, D, t_off, g64, m64, Xf, gf, mf);
+        cudaError_t e = launch_pdl(rod_forces_fused_kernel, dim3(L.n_chunks), dim3(kRodChunk), 0, s,
+                                   L, X, D, t_off, g64, m64, Xf, gf, mf);
+        if (e != cudaSuccess) return e;
     } else {
-        rod_segment_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, D, t_off);
-        rod_node_kernel<<<nblk(L.N, 128), 128, 0, s>>>(L, X, g64, m64, Xf, gf, mf);
+        cudaError_t e = launch_pdl(rod_segment_kernel, dim3(nblk(L.N, 128)), dim3(128), 0, s, L, X, D, t_off);
+        if (e == cudaSuccess)
+            e = launch_pdl(rod_node_kernel, dim3(nblk(L.N, 128)), dim3(128), 0, s, L, X, g64, m64, Xf, gf, mf);
+        if (e != cudaSuccess) return e;
     }
     if (L.p.lj_eps > 0.0) {
         const dim3 grid(nblk(L.nodes_per_inst, kLJTile), L.N / L.nodes_per_inst);
-        rod_lj_kernel<<<grid, kLJTile, 0, s>>>(L, X, g64, gf);
+        return launch_pdl(rod_lj_kernel, grid, dim3(kLJTile), 0, s, L, X, g64, gf);
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 cudaError_t launch_rod_update(const RodLaunch& L, const double* X0, const double* D0,
@@ -792,8 +801,8 @@ cudaError_t launch_rod_update(const RodLaunch& L, const double* X0, const double
                               bool bump_step, cudaStream_t s)
 {
     if (L.N == 0) return cudaSuccess;
-    rod_update_kernel<float><<<nblk(L.N, 128), 128, 0, s>>>(L, X0, D0, u, w, h, X1, D1, bump_step ? 1 : 0);
-    return cudaGetLastError();
+    return launch_pdl(rod_update_kernel<float>, dim3(nblk(L.N, 128)), dim3(128), 0, s, L, X0, D0, u, w,
+                      h, X1, D1, bump_step ? 1 : 0);
 }
 
 cudaError_t launch_rod_update64(const RodLaunch& L, const double* X0, const double* D0,
@@ -801,8 +810,8 @@ cudaError_t launch_rod_update64(const RodLaunch& L, const double* X0, const doub
                                 double* D1, bool bump_step, cudaStream_t s)
 {
     if (L.N == 0) return cudaSuccess;
-    rod_update_kernel<double><<<nblk(L.N, 128), 128, 0, s>>>(L, X0, D0, u, w, h, X1, D1, bump_step ? 1 : 0);
-    return cudaGetLastError();
+    return launch_pdl(rod_update_kernel<double>, dim3(nblk(L.N, 128)), dim3(128), 0, s, L, X0, D0, u,
+                      w, h, X1, D1, bump_step ? 1 : 0);
 }
 
 cudaError_t launch_segment_table(int N, const int2* node_info, double wave_k, double Lrod,
