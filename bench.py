@@ -483,7 +483,8 @@ def run_large_system(args):
 def run_fp32_peak(args):
     """The FP32 FMA pipe's throughput on this GPU (mrs_fma_probe): scalar FFMA, packed FFMA2 and
     the two interleaved, against the nominal 2 x 128 lanes x SMs x maximum SM clock, with the SM
-    clock sampled during the runs."""
+    clock sampled during the runs; and the FP64 pipe's, with all lanes of each warp active and
+    with one."""
     import torch
     from paper_2604_12083_gb300 import build as B, mrs
     B.build()
@@ -491,7 +492,8 @@ def run_fp32_peak(args):
     clk = ClockSampler(0)
     clk.start()
     res = {}
-    for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "ffma_ffma2_interleaved"), (3, "dfma_fp64")):
+    for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "ffma_ffma2_interleaved"), (3, "dfma_fp64"),
+                       (4, "dfma_fp64_one_lane_per_warp")):
         best = None
         for _ in range(5):
             tf, ms = mrs.fma_probe(0, kind, (1 << 18) if kind < 3 else (1 << 13))
@@ -510,6 +512,9 @@ def run_fp32_peak(args):
     for k, v in res.items():
         if not k.startswith("dfma"):
             v["frac_of_nominal"] = v["tflops"] / peak
+    # a DFMA costs the same whatever the active mask when this ratio is near 32
+    res["dfma_all_lanes_over_one_lane"] = (res["dfma_fp64"]["tflops"]
+                                           / res["dfma_fp64_one_lane_per_warp"]["tflops"])
     print(json.dumps({"case": "fp32_peak", "nominal_tflops": peak, "sms": sms,
                       "nominal_basis": "2 x 128 FP32 lanes x SMs x max SM clock", **res,
                       "clocks": clocks}), flush=True)

@@ -114,7 +114,9 @@ MRS_API int mrs_ctx_set_sym_pass_bytes(mrs_ctx* ctx, size_t bytes);
 /* Measurement aid (the paper has no counterpart): FP32 FMA-pipe throughput of the device, in
  * TFLOP/s (2 flops per lane FMA), for kind 0: scalar FFMA, 1: packed FFMA2 (fma.rn.f32x2, the
  * form the pair-sum kernels use), 2: the two interleaved, 3: float64 DFMA (the pipe the rod
- * kernels are bound by).  One launch in which every thread runs 8 independent chains of `iters`
+ * kernels are bound by), 4: float64 DFMA on lane 0 of each warp only (the flops of that one lane
+ * are counted; kind 3 / kind 4 near 32 means a DFMA costs the same whatever the active mask).
+ * One launch in which every (active) thread runs 8 independent chains of `iters`
  * steps (two FP32 lane FMAs, or one DFMA, per chain and step): warps_per_scheduler = 0 fills
  * every thread slot of the device; w >= 1 runs w warps on each scheduler of each SM (the
  * pair-sum kernel runs 2).  Timed with CUDA events after a warm-up launch; *ms (may be NULL)

@@ -5,7 +5,9 @@
 // FP32 peak 2 x 128 lanes x SMs x clock.  This kernel measures what the FMA pipe sustains on
 // the device for three instruction streams: scalar FFMA, packed FFMA2 (fma.rn.f32x2, two lanes
 // per instruction, the form the pair-sum kernels use) and the two interleaved one to one; and
-// what the float64 pipe sustains for DFMA (the rod kernels are bound by it).
+// what the float64 pipe sustains for DFMA (the rod kernels are bound by it), with every lane of a
+// warp active or only lane 0: the second tells whether the pipe's cost per warp instruction
+// depends on the active mask (on GB300 it does not: one lane costs what 32 do).
 // Every thread runs 8 independent dependency chains (enough to cover the pipe latency at 8
 // warps per scheduler), so the count is issue- and pipe-bound, not latency-bound.
 #include "mrs_internal.h"
@@ -24,9 +26,11 @@ __device__ __forceinline__ float fma_scalar(float x, float a, float b)
     return y;
 }
 
-// float64: 8 independent DFMA chains per thread
-__global__ void __launch_bounds__(kProbeBlock) dfma_probe_kernel(float* out, int iters, double a, double b)
+// float64: 8 independent DFMA chains per thread, on the first `lanes` lanes of every warp
+__global__ void __launch_bounds__(kProbeBlock) dfma_probe_kernel(float* out, int iters, int lanes, double a,
+                                                                 double b)
 {
+    if ((int)(threadIdx.x & 31) >= lanes) return;
     double x[kProbeChains];
 #pragma unroll
     for (int c = 0; c < kProbeChains; ++c) x[c] = threadIdx.x * 1e-9 + blockIdx.x * 1e-7 + c;
@@ -81,7 +85,8 @@ extern "C" int mrs_fma_probe(int device, int kind, int iters, int warps_per_sche
                              double* tflops, float* ms)
 {
     clear_error();
-    MRS_REQUIRE(kind >= 0 && kind <= 3, "kind must be 0 (FFMA), 1 (FFMA2), 2 (mixed) or 3 (DFMA)");
+    MRS_REQUIRE(kind >= 0 && kind <= 4,
+                "kind must be 0 (FFMA), 1 (FFMA2), 2 (mixed), 3 (DFMA) or 4 (DFMA on one lane per warp)");
     MRS_REQUIRE(iters >= 1 && iters <= (1 << 24), "iters must be in 1..2^24");
     MRS_REQUIRE(warps_per_scheduler >= 0 && warps_per_scheduler <= 16,
                 "warps_per_scheduler must be in 0..16");
@@ -106,7 +111,7 @@ extern "C" int mrs_fma_probe(int device, int kind, int iters, int warps_per_sche
         if (kind == 0) fma_probe_kernel<0><<<blocks, threads>>>(out, it, 0.999f, 1e-3f);
         else if (kind == 1) fma_probe_kernel<1><<<blocks, threads>>>(out, it, 0.999f, 1e-3f);
         else if (kind == 2) fma_probe_kernel<2><<<blocks, threads>>>(out, it, 0.999f, 1e-3f);
-        else dfma_probe_kernel<<<blocks, threads>>>(out, it, 0.999, 1e-3);
+        else dfma_probe_kernel<<<blocks, threads>>>(out, it, kind == 3 ? 32 : 1, 0.999, 1e-3);
         return cudaGetLastError();
     };
     if (!e) e = launch(iters / 8 + 1);   // warm-up
@@ -124,7 +129,9 @@ extern "C" int mrs_fma_probe(int device, int kind, int iters, int warps_per_sche
         return MRS_ECUDA;
     }
     // every chain step is two FP32 lane FMAs (two flops each) in kinds 0..2, one DFMA in kind 3
-    const double flops = (kind == 3 ? 2.0 : 4.0) * kProbeChains * (double)iters * blocks * threads;
+    // and kind 4; kind 4 counts the active lanes only (one per warp)
+    const double lanes = kind == 4 ? (double)blocks * (threads / 32) : (double)blocks * threads;
+    const double flops = (kind >= 3 ? 2.0 : 4.0) * kProbeChains * (double)iters * lanes;
     *tflops = flops / (t * 1e-3) / 1e12;
     if (ms) *ms = t;
     return MRS_OK;

@@ -262,7 +262,8 @@ def mrs_reserve(ctx: Context, offsets, mu, eps, eps_per_sys=None, precision=MRS_
 
 def fma_probe(device, kind, iters=1 << 16, warps_per_scheduler=0):
     """``mrs_fma_probe``: (TFLOP/s, ms) of the FP32 FMA pipe for kind 0 (FFMA), 1 (FFMA2),
-    2 (interleaved), or of the FP64 pipe (kind 3); warps_per_scheduler 0 fills the device."""
+    2 (interleaved), or of the FP64 pipe (kind 3: all lanes; kind 4: lane 0 of each warp, its
+    flops only); warps_per_scheduler 0 fills the device."""
     tf, ms = ctypes.c_double(), ctypes.c_float()
     _check(lib().mrs_fma_probe(int(device), int(kind), int(iters), int(warps_per_scheduler),
                                ctypes.byref(tf), ctypes.byref(ms)))

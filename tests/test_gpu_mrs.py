@@ -612,9 +612,11 @@ def test_fma_probe_reports_pipe_throughput(ctx):
         assert ms > 0 and 0.1 * nominal < tf < 1.1 * nominal, (kind, tf, nominal)
     tf, ms = mrs.fma_probe(0, 3, 1 << 10)        # float64: a small fraction of the FP32 rate
     assert ms > 0 and 0.0 < tf < 0.2 * nominal, tf
+    tf1, ms1 = mrs.fma_probe(0, 4, 1 << 10)      # float64 on one lane per warp: counts 1/32
+    assert ms1 > 0 and 0.0 < tf1 < tf, (tf1, tf)  # of the lanes, so never above all 32 lanes
     tf2, _ = mrs.fma_probe(0, 1, 1 << 12, 2)     # 2 warps per scheduler, as the pair kernel
     assert 0.1 * nominal < tf2 < 1.1 * nominal, tf2
     with pytest.raises(mrs.MrsError):
-        mrs.fma_probe(0, 4, 16)
+        mrs.fma_probe(0, 5, 16)
     with pytest.raises(mrs.MrsError):
         mrs.fma_probe(0, 1, 16, 17)
