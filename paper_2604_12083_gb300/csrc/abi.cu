@@ -52,16 +52,21 @@ int default_ordered_config(int n_sys, const int64_t* offsets)
     // (512-target tiles) for systems of tens of thousands of points; when most points sit in
     // systems of at most 8192 points, for a few systems 256 threads x 1 target with the source
     // loop unrolled twice (a single 4096-point system: 41 us against 50 us with 512-target
-    // tiles), or 128 threads x 1 target when no system exceeds 1536 points (1024 points: 10.3
-    // against 12.4 us), and 64 threads x 4 targets (256-target tiles, 8 CTAs per SM) for many
-    // (64 systems of 4096 points: 1.69 ms against 1.77 ms).  mrs_autotune overrides all of them.
+    // tiles), or the cluster kernel when no system exceeds 2560 points: 32-target tiles with 8
+    // source groups up to 1536 points (per call from a CUDA graph, 51 / 204 / 612 / 1275
+    // points: 3.0 / 3.0 / 4.2 / 7.2 us against 5.3 / 5.9 / 8.0 / 12.4 with the persistent
+    // kernel's 128-target tiles), 64-target tiles with 4 groups above (2048 points: 12.3
+    // against 14.3 us); 64 threads x 4 targets (256-target tiles, 8 CTAs per SM) for many
+    // systems (64 systems of 4096 points: 1.69 ms against 1.77 ms).  mrs_autotune overrides
+    // all of them.
     int64_t small = 0, total = offsets[n_sys], largest = 0;
     for (int s = 0; s < n_sys; ++s) {
         const int64_t ns = offsets[s + 1] - offsets[s];
         if (ns <= 8192) small += ns;
         largest = std::max(largest, ns);
     }
-    if (total > 0 && small * 2 > total) return n_sys >= 16 ? 8 : largest <= 1536 ? 13 : 14;
+    if (total > 0 && small * 2 > total)
+        return n_sys >= 16 ? 8 : largest <= 1536 ? 27 : largest <= 2560 ? 28 : 14;
     return 9;
 }
 
@@ -276,7 +281,7 @@ int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, doubl
     p->config = cfg;
     p->ocfg = kConfigs[cfg].sym ? default_ordered_config(n_sys, offsets) : cfg;
     const KernelConfig kc = kConfigs[p->ocfg];
-    p->TM = kc.threads * kc.tpt;
+    p->TM = tile_targets(kc);
     std::vector<TileDesc> tiles;
     long long W = 0;
     for (int s = 0; s < n_sys; ++s) {
@@ -320,9 +325,31 @@ int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, doubl
     }
     long long max_nu = 0;
     for (const TileDesc& T : tiles) max_nu = std::max<long long>(max_nu, T.nu);
-    const long long P = ordered_ctas((long long)ctx->num_sms * occ * std::max(1, kc.over), W, max_nu);
+    long long P = 0;
+    if (kc.cluster) {
+        // one cluster per tile: the largest size (at most the configuration's cap and the
+        // largest tile's units) for which the clusters of all tiles are resident at once, so
+        // that no cluster waits for a second wave; size 1 if none
+        const bool comp = precision == MRS_F32_COMP;
+        int cl = (int)std::max<long long>(1, std::min<long long>(kc.cluster, max_nu));
+        for (;; --cl) {
+            int mc = 0;
+            const int cst = cluster_setup_f32(p->ocfg, comp, cl, &mc);
+            if (cst != MRS_OK) cudaGetLastError();   // a refused cluster shape is not an error of the plan
+            if (cst == MRS_OK && mc >= 1 && (mc >= p->n_tiles || cl == 1)) break;
+            if (cl == 1) {
+                plan_free(p);
+                set_error("no cluster of config %d fits on the device", p->ocfg);
+                return MRS_ECUDA;
+            }
+        }
+        p->cl = cl;
+        P = (long long)p->n_tiles * cl;
+    } else {
+        P = ordered_ctas((long long)ctx->num_sms * occ * std::max(1, kc.over), W, max_nu);
+    }
     p->P = (int)P;
-    const size_t part_floats = (size_t)2 * P * 6 * p->TM;
+    const size_t part_floats = kc.cluster ? 1 : (size_t)2 * P * 6 * p->TM;
     if ((st = dev_alloc(&p->d_tiles, tiles.size())) || (st = dev_alloc(&p->d_sc, sc.size())) ||
         (st = dev_alloc(&p->d_partial, part_floats)) || (st = dev_alloc(&p->d_counters, tiles.size()))) {
         plan_free(p);
@@ -403,6 +430,7 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
         L.counters = p->d_counters;
         L.err = p->ctx->d_err;
         L.n_points = p->n_points;
+        L.cl = p->cl;
         if (p->sym_config >= 0 && (Xt == nullptr || Xt == X)) {
             SymLaunch S;
             S.tiles = p->d_stiles;
@@ -607,7 +635,8 @@ int mrs_plan_scratch(const mrs_plan* plan, int* passes, size_t* scratch_bytes)
     const bool sym = plan->precision != MRS_F64 && plan->sym_config >= 0;
     if (passes) *passes = sym ? (int)plan->passes.size() : 1;
     if (scratch_bytes) {
-        size_t b = (size_t)2 * plan->P * 6 * plan->TM * sizeof(float);   // ordered slots
+        // ordered slots (none for a cluster configuration: its partials stay on chip)
+        size_t b = plan->cl ? 0 : (size_t)2 * plan->P * 6 * plan->TM * sizeof(float);
         if (sym) {
             long long seg = 0, units = 0;
             for (const SymPass& ps : plan->passes) {

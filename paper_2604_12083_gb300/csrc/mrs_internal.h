@@ -31,21 +31,36 @@ __device__ __forceinline__ void pdl_wait()
 }
 #endif
 
+// cluster > 0: the grid is also cut into thread-block clusters of `cluster` CTAs along x.
 template <typename... Params, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, Args... args)
+inline cudaError_t launch_pdl_cl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t s, int cluster, Args... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (cluster > 0) {
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = (unsigned)cluster;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        cfg.numAttrs = 2;
+    }
+    cfg.attrs = attr;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args)
+{
+    return launch_pdl_cl(kernel, grid, block, smem, s, 0, args...);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -130,7 +145,19 @@ struct KernelConfig {
     int sym;       // 1: each unordered pair once (targets = sources only; mrs_sym.cu)
     int over;      // CTAs launched per resident CTA slot (0 or 1: one wave; > 1: the hardware
                    // block scheduler hands the later CTAs to SMs as earlier ones finish)
+    int cluster;   // > 0: the cluster kernel (mrs_f32_cluster, ordered, TPT = 1): one
+                   // thread-block cluster of up to `cluster` CTAs per target tile, each CTA over
+                   // a share of the tile's sources, partials summed through distributed shared
+                   // memory (small systems: no scratch, no counters, no finishing CTA)
+    int groups;    // cluster kernel: source groups per CTA (threads = targets per tile x groups;
+                   // each group sweeps every groups-th 4-source block of the CTA's sources)
 };
+
+// Targets per tile of a configuration.
+inline int tile_targets(const KernelConfig& k)
+{
+    return k.threads * k.tpt / (k.groups > 1 ? k.groups : 1);
+}
 
 // Configurations compiled into the library (index = plan config id).
 extern const KernelConfig kConfigs[];
@@ -152,10 +179,14 @@ struct MrsLaunch {
     int* counters;        // [n_tiles], zero between launches
     long long n_points;   // points of the arrays (index checks of the debug build)
     unsigned int* err;    // device error word: bit 0 = a non-finite output was written
+    int cl = 0;           // cluster kernel: CTAs per cluster (P = n_tiles * cl); else unused
 };
 
 cudaError_t launch_mrs_f32(int config, bool comp, const MrsLaunch& L, cudaStream_t s);
 int occupancy_f32(int config, bool comp, int* ctas_per_sm);
+// Cluster configurations: allow clusters of more than 8 CTAs for the kernel and return in
+// *max_clusters how many clusters of `cl` CTAs can be resident at once (0: none fits).
+int cluster_setup_f32(int config, bool comp, int cl, int* max_clusters);
 
 // ---------------------------------------------------------------------------------------------
 // Symmetric pair sum (targets = sources): every unordered pair {i, j} of a system is evaluated
@@ -291,6 +322,7 @@ struct mrs_plan {
     // float32 persistent path
     int P = 0;
     int TM = 0;
+    int cl = 0;                   // cluster configuration: CTAs per cluster (P = n_tiles * cl)
     long long W = 0;
     int n_tiles = 0;
     mrs::TileDesc* d_tiles = nullptr;

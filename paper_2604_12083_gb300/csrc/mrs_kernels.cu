@@ -446,6 +446,185 @@ mrs_f32_persistent(const MrsLaunch L)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Cluster kernel for small systems (KernelConfig::cluster > 0).  One thread-block cluster of
+// L.cl CTAs per target tile of BLOCK targets (one per thread); CTA r of the cluster sweeps the
+// units [nu r / cl, nu (r+1) / cl) of the tile's sources with the packed inner loop and the
+// per-chunk Kahan folding of mrs_f32_persistent, and leaves its partial (sum - compensation,
+// one float per target and component) in its own shared memory.  After a cluster barrier, CTA r
+// reduces targets [r tpr, (r+1) tpr) of the tile, tpr = ceil(BLOCK / cl): it reads the partial
+// of every CTA of the cluster through distributed shared memory (mapa + ld.shared::cluster) and
+// sums them in rank order with float32 Kahan, as the persistent kernel's finishing CTA sums its
+// slots.  A second barrier keeps every CTA resident until its partials have been read.  For a
+// system of a few hundred to a few thousand points this replaces the scratch slots in global
+// memory, the atomic tile counter and the finishing CTA's reads with on-chip traffic: the call
+// is then a load of the sources, the sweep and two cluster barriers.
+//
+// Every thread of every CTA reaches both barriers: nothing returns early (a CTA with no units
+// contributes zero partials; the debug build's index checks skip work instead of returning).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_index()
+{
+    unsigned c;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(c));
+    return c;
+}
+
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// float at shared-memory address `p` (this CTA's) in the shared memory of CTA `rank`
+__device__ __forceinline__ float ld_cluster_f32(const float* p, unsigned rank)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    unsigned ra;
+    float v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+constexpr int kMaxCluster = 16;
+
+template <int TM, int G, bool COMP, int UNROLL>
+__global__ void __launch_bounds__(TM * G) mrs_f32_cluster(const MrsLaunch L)
+{
+    pdl_wait();
+    constexpr int BLOCK = TM * G;
+    __shared__ __align__(16) float sflat[kChunk * 9];
+    __shared__ float sgrp[G > 1 ? G * 6 * TM : 1];   // each group's partial: [group][component][target]
+    __shared__ float spart[6 * TM];                  // the CTA's partial: [component][target]
+
+    const int tid = threadIdx.x;
+    const int lt = tid % TM, g = tid / TM;   // target of the tile, source group
+    const int cl = L.cl;
+    const int ti = (int)cluster_index();
+    const int r = (int)cluster_rank();
+    bool ok = true;
+#if MRS_DEBUG_BOUNDS
+    ok = ti >= 0 && ti < L.n_tiles && cl >= 1 && cl <= kMaxCluster && r < cl;
+    if (ok) ok = ordered_tile_ok(L.tiles[ti], TM, L.n_points);
+    if (!ok && tid == 0) atomicOr(L.err, MRS_FLAG_BOUNDS);
+#endif
+    const TileDesc T = L.tiles[ok ? ti : 0];
+    const SysConst sc = L.sc[ok ? T.sys : 0];
+    const int ua = (int)((long long)T.nu * r / cl), ub = (int)((long long)T.nu * (r + 1) / cl);
+
+    float xt[3];
+    {
+        const long long gi = (long long)T.t0 + (lt < T.tn ? lt : T.tn - 1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xt[c] = L.Xt[gi * 3 + c];
+    }
+    float acc[6], ks[6], kc[6];
+    float2 acc2[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        acc[q] = ks[q] = kc[q] = 0.f;
+        acc2[q] = make_float2(0.f, 0.f);
+    }
+    const long long jbeg = (long long)T.s0 + (long long)ua * kUnitSources;
+    const long long jend = ok ? (long long)T.s0 + min((long long)ub * kUnitSources, (long long)T.sn) : jbeg;
+    const float2 e2 = f2(sc.e2), c1 = f2(sc.c1), c2 = f2(sc.c2), c3 = f2(sc.c3), c5 = f2(sc.c5);
+    const float2 xn[3] = {f2(xt[0]), f2(xt[1]), f2(xt[2])};
+    for (long long j0 = jbeg; j0 < jend; j0 += kChunk) {
+        const int cnt = (int)min((long long)kChunk, jend - j0);
+        const int cntp = (cnt + 3) & ~3;
+        __syncthreads();   // the previous chunk is no longer read
+        const float* gX = L.X + j0 * 3;
+        const float* gf = L.f + j0 * 3;
+        const float* gn = L.n + j0 * 3;
+        for (int idx = tid; idx < cnt * 3; idx += BLOCK) {
+            const int sidx = idx / 3, c = idx - sidx * 3;
+            sflat[c * kChunk + sidx] = __ldg(gX + idx);
+            sflat[(3 + c) * kChunk + sidx] = __ldg(gf + idx);
+            sflat[(6 + c) * kChunk + sidx] = __ldg(gn + idx);
+        }
+        for (int sidx = cnt + tid; sidx < cntp; sidx += BLOCK) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) sflat[c * kChunk + sidx] = 0.f;   // zero source: adds 0
+        }
+        __syncthreads();
+        // group g takes the 4-source blocks g, g + G, g + 2G, ... of the chunk
+#pragma unroll UNROLL
+        for (int j = 4 * g; j < cntp; j += 4 * G) {
+            float4 v[9];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) v[c] = *reinterpret_cast<const float4*>(&sflat[c * kChunk + j]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float2 s9[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c)
+                    s9[c] = h == 0 ? make_float2(v[c].x, v[c].y) : make_float2(v[c].z, v[c].w);
+                pair_f32x2<false>(xn[0], xn[1], xn[2], s9[0], s9[1], s9[2], s9[3], s9[4], s9[5], s9[6],
+                                  s9[7], s9[8], e2, c1, c2, c3, c5, acc2);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            acc[q] = __fadd_rn(acc[q], __fadd_rn(acc2[q].x, acc2[q].y));
+            acc2[q] = make_float2(0.f, 0.f);
+            if (COMP) {   // Kahan fold of this chunk's partial
+                kahan_add(ks[q], kc[q], acc[q]);
+                acc[q] = 0.f;
+            }
+        }
+    }
+    if (G > 1) {
+        // the groups' partials summed in group order (float32 Kahan) into the CTA's partial
+#pragma unroll
+        for (int q = 0; q < 6; ++q) sgrp[(g * 6 + q) * TM + lt] = COMP ? __fsub_rn(ks[q], kc[q]) : acc[q];
+        __syncthreads();
+        for (int e = tid; e < 6 * TM; e += BLOCK) {
+            float tot = 0.f, cmp = 0.f;
+#pragma unroll
+            for (int gg = 0; gg < G; ++gg) kahan_add(tot, cmp, sgrp[gg * 6 * TM + e]);
+            spart[e] = __fsub_rn(tot, cmp);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) spart[q * TM + lt] = COMP ? __fsub_rn(ks[q], kc[q]) : acc[q];
+    }
+
+    cluster_barrier();   // every CTA's partials are written and visible to the cluster
+
+    const int tpr = (TM + cl - 1) / cl;
+    const int lo = r * tpr, hi = min(TM, lo + tpr);
+    for (int e = tid; e < (hi - lo) * 6; e += BLOCK) {
+        const int li = lo + e / 6, q = e - (e / 6) * 6;
+        const float* src = spart + q * TM + li;
+        float v[kMaxCluster];
+#pragma unroll
+        for (int k = 0; k < kMaxCluster; ++k) v[k] = k < cl ? ld_cluster_f32(src, (unsigned)k) : 0.f;
+        float tot = 0.f, cmp = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMaxCluster; ++k)
+            if (k < cl) kahan_add(tot, cmp, v[k]);
+        if (ok && li < T.tn) {
+            const long long gi = (long long)T.t0 + li;
+            const float val = __fsub_rn(tot, cmp) * sc.scale;
+            if (!isfinite(val)) atomicOr(L.err, 1u);
+            if (q < 3) L.u[gi * 3 + q] = val; else L.w[gi * 3 + q - 3] = val;
+        }
+    }
+
+    // no CTA leaves while another still reads its partials; the reads above have completed
+    // (their values are consumed), so the arrival needs no release ordering
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\t"
+                 "barrier.cluster.wait.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
 // Configuration table and dispatch.
 // ---------------------------------------------------------------------------------------------
 const KernelConfig kConfigs[] = {
@@ -458,6 +637,9 @@ const KernelConfig kConfigs[] = {
     {128, 6, 1, 1, 1, 1}, {128, 8, 1, 1, 1, 1}, {64, 6, 1, 1, 1, 1},
     // ... the last three launched as 2, 4 and 8 waves of CTAs (KernelConfig::over)
     {64, 6, 1, 1, 1, 1, 2}, {64, 6, 1, 1, 1, 1, 4}, {64, 6, 1, 1, 1, 1, 8},
+    // cluster kernel (small systems): 256 threads per CTA as 32 targets x 8 source groups and
+    // as 64 targets x 4, clusters of up to 16 CTAs
+    {256, 1, 1, 1, 0, 0, 0, 16, 8}, {256, 1, 1, 1, 0, 0, 0, 16, 4},
 };
 const int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 
@@ -503,15 +685,76 @@ static int occ_t(int* n)
     default: break;                                                                       \
     }
 
+template <int TM, int G, bool COMP, int UNROLL>
+static cudaError_t launch_cl_t(const MrsLaunch& L, cudaStream_t s)
+{
+    return launch_pdl_cl(mrs_f32_cluster<TM, G, COMP, UNROLL>, dim3(L.P), dim3(TM * G), 0, s, L.cl, L);
+}
+
+template <int TM, int G, bool COMP, int UNROLL>
+static int occ_cl_t(int* n)
+{
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, mrs_f32_cluster<TM, G, COMP, UNROLL>,
+                                                                  TM * G, 0);
+    return e == cudaSuccess ? MRS_OK : MRS_ECUDA;
+}
+
+template <int TM, int G, bool COMP, int UNROLL>
+static int setup_cl_t(int cl, int* n)
+{
+    *n = 0;
+    if (cl < 1 || cl > kMaxCluster) return MRS_EINVAL;
+    cudaError_t e = cudaFuncSetAttribute(mrs_f32_cluster<TM, G, COMP, UNROLL>,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cl);
+        cfg.blockDim = dim3(TM * G);
+        cudaLaunchAttribute a[1];
+        a[0].id = cudaLaunchAttributeClusterDimension;
+        a[0].val.clusterDim.x = (unsigned)cl;
+        a[0].val.clusterDim.y = 1;
+        a[0].val.clusterDim.z = 1;
+        cfg.attrs = a;
+        cfg.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(n, mrs_f32_cluster<TM, G, COMP, UNROLL>, &cfg);
+    }
+    return e == cudaSuccess ? MRS_OK : MRS_ECUDA;
+}
+
+#define MRS_CASE_CL(id, TM, G, U, FN, ...) \
+    case id:                              \
+        return comp ? FN<TM, G, true, U>(__VA_ARGS__) : FN<TM, G, false, U>(__VA_ARGS__);
+#define MRS_DISPATCH_CL(cfg, comp, FN, ...)          \
+    switch (cfg) {                                   \
+        MRS_CASE_CL(27, 32, 8, 1, FN, __VA_ARGS__)   \
+        MRS_CASE_CL(28, 64, 4, 1, FN, __VA_ARGS__)   \
+    default: break;                                  \
+    }
+
 cudaError_t launch_mrs_f32(int config, bool comp, const MrsLaunch& L, cudaStream_t s)
 {
+    if (config >= 0 && config < kNumConfigs && kConfigs[config].cluster) {
+        MRS_DISPATCH_CL(config, comp, launch_cl_t, L, s);
+        return cudaErrorInvalidValue;
+    }
     MRS_DISPATCH(config, comp, launch_t, L, s);
     return cudaErrorInvalidValue;
 }
 
 int occupancy_f32(int config, bool comp, int* ctas_per_sm)
 {
+    if (config >= 0 && config < kNumConfigs && kConfigs[config].cluster) {
+        MRS_DISPATCH_CL(config, comp, occ_cl_t, ctas_per_sm);
+        return MRS_EINVAL;
+    }
     MRS_DISPATCH(config, comp, occ_t, ctas_per_sm);
+    return MRS_EINVAL;
+}
+
+int cluster_setup_f32(int config, bool comp, int cl, int* max_clusters)
+{
+    MRS_DISPATCH_CL(config, comp, setup_cl_t, cl, max_clusters);
     return MRS_EINVAL;
 }
 

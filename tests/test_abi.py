@@ -59,12 +59,13 @@ def test_errors_without_gpu_are_reported_not_fatal(libpath):
 
 
 def test_config_table_host_queries(libpath):
-    """The configuration table answers without a device: ordered configurations first, then
-    the symmetric ones (each unordered pair evaluated once); out-of-range ids are rejected."""
+    """The configuration table answers without a device: the persistent ordered
+    configurations 0..16, the symmetric ones (each unordered pair evaluated once) 17..26, then
+    the ordered cluster ones; out-of-range ids are rejected."""
     from paper_2604_12083_gb300 import mrs
     n = mrs.plan_config_count()
     flags = [mrs.plan_config_symmetric(c) for c in range(n)]
-    assert not any(flags[:17]) and all(flags[17:]) and len(flags) > 17
+    assert n == 29 and not any(flags[:17]) and all(flags[17:27]) and not any(flags[27:])
     assert mrs.lib().mrs_plan_config_symmetric(n) == -1
     assert mrs.lib().mrs_plan_config_symmetric(-1) == -1
     with pytest.raises(mrs.MrsError):

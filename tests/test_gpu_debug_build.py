@@ -34,7 +34,7 @@ X, f, n = (torch.from_numpy(a).cuda() for a in (p.X, p.f, p.n))
 nz = [s for s in range(len(p.offsets) - 1) if p.offsets[s] < p.offsets[s + 1]]
 for pass_bytes in (192 << 20, 3 * 768):
     ctx.set_sym_pass_bytes(pass_bytes)
-    configs = range(mrs.plan_config_count()) if pass_bytes > 4096 else range(17, mrs.plan_config_count())
+    configs = [c for c in range(mrs.plan_config_count()) if pass_bytes > 4096 or mrs.plan_config_symmetric(c)]
     for cfg in configs:
         pl = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=mrs.MRS_F32_COMP, config=cfg)
         u, w = torch.full_like(X, float("nan")), torch.full_like(X, float("nan"))

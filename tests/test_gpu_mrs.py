@@ -98,8 +98,10 @@ def ragged_batch():
     return W.MRSProblem("ragged", off, f32(Xs), f32(fs), f32(ns), eps, 1.3)
 
 
-N_CONFIGS = 27          # ordered configurations 0..16, symmetric (pair-reuse) 17..26
+N_CONFIGS = 29          # ordered 0..16, symmetric (pair-reuse) 17..26, ordered cluster 27..28
 SYM_CONFIGS = list(range(17, 27))
+CLUSTER_CONFIGS = [27, 28]
+CLUSTER_TM = {27: 32, 28: 64}   # 256 threads as 32 targets x 8 and 64 x 4 source groups
 
 
 @pytest.mark.parametrize("config", list(range(N_CONFIGS)))
@@ -184,7 +186,8 @@ def test_small_system_split_cap(ctx, orc, config):
         pl.close()
         if not mrs.plan_config_symmetric(info["config"]):
             ci = mrs.plan_config_info(ctx, info["config"])
-            tiles = -(-M // (ci["threads"] * ci["targets_per_thread"]))
+            TM = CLUSTER_TM.get(info["config"], ci["threads"] * ci["targets_per_thread"])
+            tiles = -(-M // TM)
             assert info["grid"] >= 1
             assert info["grid"] <= 16 * tiles or info["work_units"] >= 4 * info["grid"], (M, info)
             if M <= 2048:                       # a few units per CTA at most: the cap binds
@@ -354,6 +357,54 @@ def test_config_table_size(ctx):
     for c in range(N_CONFIGS):
         info = mrs.plan_config_info(ctx, c)
         assert info["ctas_per_sm"] >= 1
+        assert mrs.plan_config_symmetric(c) == (c in SYM_CONFIGS)
+
+
+@pytest.mark.parametrize("config", CLUSTER_CONFIGS)
+@pytest.mark.parametrize("shape", [(1, 51), (4, 51), (12, 51), (25, 51), (1, 4099)])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_cluster_small_systems(ctx, orc, config, shape, precision):
+    """The cluster kernel on single systems of the paper's sizes (1, 4, 12, 25 rods of 51
+    points) and a ragged 4099-point one: every target against the oracle (field L2 and
+    per-target bounds), a second call bit-identical (the cluster sums its CTAs' partials in a
+    fixed order), no scratch slots, one cluster of at most 16 CTAs per tile."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    n_fil, M = shape
+    p = W.single_system(seed=70 + n_fil, n_fil=n_fil, M=M, box=3.0)
+    N = n_fil * M
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu)
+    X, f, n = dev(p.X), dev(p.f), dev(p.n)
+    pl = mrs.Plan(ctx, p.offsets, p.mu, 0.0, eps_per_sys=p.eps, precision=precision, config=config)
+    outs = []
+    for _ in range(2):
+        u, w = torch.full_like(X, float("nan")), torch.full_like(X, float("nan"))
+        pl.execute(X, f, n, u, w)
+        torch.cuda.synchronize()
+        outs.append((u.cpu().numpy(), w.cpu().numpy()))
+    info = pl.info()
+    sc = pl.scratch()
+    pl.close()
+    (u0, w0), (u1, w1) = outs
+    assert np.array_equal(u0, u1) and np.array_equal(w0, w1)
+    u, w = u0.astype(np.float64), w0.astype(np.float64)
+    assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32, (rel_l2(u, ur), rel_l2(w, wr))
+    assert per_target_max(u, ur) < PER_TARGET and per_target_max(w, wr) < PER_TARGET
+    TM = CLUSTER_TM[config]
+    tiles = -(-N // TM)
+    assert info["grid"] % tiles == 0 and 1 <= info["grid"] // tiles <= 16, (info, tiles)
+    assert sc["passes"] == 1 and sc["bytes"] == 0
+
+
+@pytest.mark.parametrize("config", CLUSTER_CONFIGS)
+def test_cluster_separate_targets(ctx, orc, config):
+    """The cluster kernel with targets apart from the sources (a shifted copy of the points)."""
+    from paper_2604_12083_gb300 import workloads as W
+    p = W.single_system(seed=75, n_fil=12, M=51, box=3.0)
+    Xt = (p.X + np.float32(0.013)).astype(np.float32)
+    u, w = run(ctx, p, 2, config=config, Xt=Xt)
+    ur, wr = orc.mrs_velocity(p.X, p.f, p.n, p.eps[0], p.mu, xt=Xt)
+    assert rel_l2(u, ur) < TOL32 and rel_l2(w, wr) < TOL32
+    assert per_target_max(u, ur) < PER_TARGET and per_target_max(w, wr) < PER_TARGET
 
 
 def test_nonfinite_inputs_raise_the_device_flag(ctx):
@@ -442,7 +493,7 @@ def test_symmetric_passes_match_oracle(ctx, mid_system, config, precision):
     assert rel_l2(u, u1) < TOL32 and rel_l2(w, w1) < TOL32
 
 
-@pytest.mark.parametrize("config", list(range(17, N_CONFIGS)))
+@pytest.mark.parametrize("config", SYM_CONFIGS)
 def test_symmetric_passes_ragged_batch(ctx, orc, config):
     """The ragged batch with passes of three work units: passes end inside systems, span
     several small systems and hold single tiles; every system matches the oracle."""
