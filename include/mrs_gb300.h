@@ -91,12 +91,30 @@ MRS_API int mrs_ctx_num_sms(const mrs_ctx* ctx);
  * keeps the instance's state in shared memory and runs forces (with the Lennard-Jones repulsion
  * when enabled), float32 pair sum and update of every stage back to back.  The other path runs
  * every step as forces -> pair-sum plan -> update kernels replayed from captured CUDA graphs,
- * over all SMs.  mode = 1 (the default): fused for instances of at most 128 nodes, where one SM
- * per instance is the faster choice; mode = 2: fused whenever the instance fits shared memory
+ * over all SMs.  mode = 1 (the default): fused for instances of at most 128 nodes in a batch of
+ * more than 4096 nodes (e.g. the slices of a Parareal solve), where one SM per instance is the
+ * faster choice; smaller batches take the graphs, whose warp-cooperative force and update
+ * kernels (mrs_ctx_set_rod_force_kernel) are faster there; mode = 2: fused whenever the
+ * instance fits shared memory
  * (at most ~600 nodes); mode = 0: never.  MRS_F64 stepping always takes the graphs.  Both paths
  * compute the same steps; results agree to float32 rounding of the pair sum.  Host only.
  * Errors: MRS_EINVAL (mode outside 0..2). */
 MRS_API int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable);
+
+/* Rod force kernel of the context (rod_forces; rod_step, parareal_run and
+ * parareal_run_pipelined on the graph path): the internal force and moment of every segment
+ * and the node force and torque (Eqs. mid_triad, F_comp_discrete, N_comp_discrete,
+ * discrete_f, discrete_n).  GB300 executes a float64 warp instruction in about 64 cycles per
+ * scheduler whatever the number of active lanes, so a segment computed by one thread costs its
+ * whole float64 path on one scheduler.  The warp-cooperative kernel spreads each segment over
+ * ten lanes (three segments per warp, a fourth warp per CTA for the preferred curvature and the
+ * node phase), which shortens the path per scheduler and uses more schedulers; the
+ * thread-per-segment kernel does the least float64 work in all.  mode = 0 (the default):
+ * warp-cooperative for batches of at most 4096 nodes, thread per segment above; 1: always one
+ * thread per segment; 2: always warp-cooperative.  Both compute the same expressions; results
+ * agree to float64 rounding.  Takes effect for calls made afterwards (captured step graphs are
+ * kept per setting).  Host only.  Errors: MRS_EINVAL (mode outside 0..2). */
+MRS_API int mrs_ctx_set_rod_force_kernel(mrs_ctx* ctx, int mode);
 
 /* Largest column-partial buffer of one pass of a symmetric pair-sum plan (configurations
  * 17..26; see mrs_plan_create), in bytes, for plans created from then on.  A plan whose column

@@ -545,6 +545,15 @@ int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable)
     return MRS_OK;
 }
 
+int mrs_ctx_set_rod_force_kernel(mrs_ctx* ctx, int mode)
+{
+    clear_error();
+    MRS_REQUIRE(ctx != nullptr, "ctx is NULL");
+    MRS_REQUIRE(mode >= 0 && mode <= 2, "mode must be 0, 1 or 2 (got %d)", mode);
+    ctx->rod_force_kernel = mode;
+    return MRS_OK;
+}
+
 int mrs_ctx_set_sym_pass_bytes(mrs_ctx* ctx, size_t bytes)
 {
     clear_error();

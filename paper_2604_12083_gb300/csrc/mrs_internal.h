@@ -364,8 +364,13 @@ struct mrs_ctx {
     // measured best kernel configurations (mrs_autotune)
     std::vector<mrs::TuneEntry> tuned;
     // rod stepping in one fused launch per call (mrs_ctx_set_fused_steps): 0 never, 1 for
-    // instances of at most kFusedAutoNodes nodes, 2 whenever the instance fits shared memory
+    // instances of at most kFusedAutoNodes nodes in batches too large for the warp-cooperative
+    // kernels, 2 whenever the instance fits shared memory
     int fused_steps = 1;
+    // rod force kernel (mrs_ctx_set_rod_force_kernel): 0 warp-cooperative for batches of at
+    // most kWarpForceMaxNodes nodes, else one thread per segment; 1 always one thread per
+    // segment; 2 always warp-cooperative
+    int rod_force_kernel = 0;
     // largest column-partial buffer (bytes) of one pass of a symmetric plan; a plan with more
     // column partials is split into passes (mrs_ctx_set_sym_pass_bytes)
     size_t sym_pass_bytes = (size_t)192 << 20;

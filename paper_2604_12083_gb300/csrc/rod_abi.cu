@@ -59,7 +59,7 @@ void rod_ws_free(RodWorkspace* ws)
     for (auto& g : ws->graphs) cudaGraphExecDestroy(g.exec);
     if (ws->cap) cudaStreamDestroy(ws->cap);
     if (ws->plan) plan_free(ws->plan);
-    void* ptrs[] = {ws->d_node_info, ws->d_chunks, ws->d_t0, ws->d_step, ws->d_FN, ws->d_Xf, ws->d_gf, ws->d_mf,
+    void* ptrs[] = {ws->d_node_info, ws->d_chunks, ws->d_wchunks, ws->d_t0, ws->d_step, ws->d_FN, ws->d_Xf, ws->d_gf, ws->d_mf,
                     ws->d_u, ws->d_w, ws->d_g64, ws->d_m64, ws->d_u64, ws->d_w64, ws->d_Xh, ws->d_Dh,
                     ws->d_segsc};
     for (void* q : ptrs) cudaFree(q);
@@ -94,17 +94,20 @@ int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int
     ws->N = ws->N1 * n_inst;
     const size_t N = (size_t)ws->N;
     std::vector<int2> info(N);
-    std::vector<int> chunks;
+    std::vector<int> chunks, wchunks;
     for (int i = 0; i < n_inst; ++i)
         for (int r = 0; r < n_rods; ++r) {
             const int M = (int)(rod_off[r + 1] - rod_off[r]);
             for (int k = 0; k < M; ++k) info[(size_t)i * ws->N1 + rod_off[r] + k] = make_int2(k, M);
             for (int c = 0; c < M; c += kRodChunk - 1)
                 chunks.push_back((int)((size_t)i * ws->N1 + rod_off[r] + c));
+            for (int c = 0; c < M; c += kWNodes) wchunks.push_back((int)((size_t)i * ws->N1 + rod_off[r] + c));
         }
     ws->n_chunks = (int)chunks.size();
+    ws->n_wchunks = (int)wchunks.size();
     int st;
     if ((st = dalloc(&ws->d_node_info, N)) || (st = dalloc(&ws->d_chunks, chunks.size())) ||
+        (ws->n_wchunks && (st = dalloc(&ws->d_wchunks, wchunks.size()))) ||
         (st = dalloc(&ws->d_t0, n_inst)) ||
         (st = dalloc(&ws->d_step, 1)) || (st = dalloc(&ws->d_FN, 6 * N)) ||
         (st = dalloc(&ws->d_Xh, 3 * N)) || (st = dalloc(&ws->d_Dh, 9 * N)) ||
@@ -128,6 +131,8 @@ int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int
     }
     cudaMemcpy(ws->d_node_info, info.data(), N * sizeof(int2), cudaMemcpyHostToDevice);
     cudaMemcpy(ws->d_chunks, chunks.data(), chunks.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (ws->n_wchunks)
+        cudaMemcpy(ws->d_wchunks, wchunks.data(), wchunks.size() * sizeof(int), cudaMemcpyHostToDevice);
     cudaMemset(ws->d_t0, 0, n_inst * sizeof(double));
     cudaMemset(ws->d_step, 0, sizeof(long long));
     if (eps > 0.0) {
@@ -171,6 +176,11 @@ RodLaunch rod_launch(const RodWorkspace* ws, const mrs_rod_params* p, double dt)
     L.FN = ws->d_FN;
     L.chunks = ws->d_chunks;
     L.n_chunks = ws->n_chunks;
+    // warp-cooperative force kernel: small batches by default (mrs_ctx_set_rod_force_kernel)
+    const int fk = ws->ctx ? ws->ctx->rod_force_kernel : 0;
+    const bool warp_forces = fk == 2 || (fk == 0 && ws->N <= kWarpForceMaxNodes);
+    L.wchunks = warp_forces && ws->n_wchunks ? ws->d_wchunks : nullptr;
+    L.n_wchunks = ws->n_wchunks;
     L.inv_L = 1.0 / p->L;
     set_pack_reference(L, ws->n_rods, ws->rod_off.data());
     L.segsc = (ws->segsc_k == p->wave_k && ws->segsc_L == p->L) ? ws->d_segsc : nullptr;
@@ -257,7 +267,7 @@ static int get_graph(RodWorkspace* ws, const mrs_rod_params* p, double* X, doubl
 {
     for (auto& g : ws->graphs) {
         if (g.X == X && g.D == D && g.scheme == scheme && g.steps == steps && g.dt == dt &&
-            std::memcmp(&g.p, p, sizeof(*p)) == 0) {
+            g.force_kernel == ws->ctx->rod_force_kernel && std::memcmp(&g.p, p, sizeof(*p)) == 0) {
             *out = g.exec;
             return MRS_OK;
         }
@@ -290,6 +300,7 @@ static int get_graph(RodWorkspace* ws, const mrs_rod_params* p, double* X, doubl
     RodWorkspace::Graph g;
     g.X = X;
     g.D = D;
+    g.force_kernel = ws->ctx->rod_force_kernel;
     g.scheme = scheme;
     g.steps = steps;
     g.dt = dt;
@@ -310,9 +321,13 @@ int rod_ws_steps(RodWorkspace* ws, const mrs_rod_params* p, double* X, double* D
     if (pst) return pst;
     // small instances: every step of every instance in one launch, the state in shared memory
     // (one CTA per instance)
+    // (by default only when the batch is too large for the warp-cooperative kernels of the
+    // graph path, which are faster for a batch of up to kWarpForceMaxNodes nodes)
     const int fmode = ws->ctx->fused_steps;
+    const int fk = ws->ctx->rod_force_kernel;
+    const bool warp_kernels = fk == 2 || (fk == 0 && ws->N <= kWarpForceMaxNodes);
     if (fmode > 0 && ws->precision != MRS_F64 && fused_fits(ws->N1) &&
-        (fmode == 2 || ws->N1 <= kFusedAutoNodes)) {
+        (fmode == 2 || (ws->N1 <= kFusedAutoNodes && !warp_kernels))) {
         const RodLaunch L = rod_launch(ws, p, dt);
         cudaError_t e = launch_rod_fine_fused(L, X, D, nsteps, scheme, p->mu, p->eps, s);
         if (e != cudaSuccess) {

@@ -16,6 +16,10 @@ struct RodLaunch {
     double* FN;                // [N][6] segment force / moment scratch (two-kernel path)
     const int* chunks;         // [n_chunks] base node of every fused-kernel chunk, or NULL
     int n_chunks;
+    // [n_wchunks] base node of every chunk of kWNodes nodes (warp-cooperative force kernel,
+    // systems of at most kWarpForceMaxNodes nodes), or NULL
+    const int* wchunks = nullptr;
+    int n_wchunks = 0;
     double inv_L;              // 1 / p.L
     // Reference point of the float32 position packs (see rod_kernels.cu): the mean of the
     // nodes ref[0..n_ref) of the instance (indices within it), weight ref_w = 1 / n_ref;
@@ -42,6 +46,11 @@ inline void set_pack_reference(RodLaunch& L, int n_rods, const int64_t* rod_off)
     L.ref_w = R > 0 ? 1.0 / R : 0.0;
 }
 constexpr int kRodChunk = 128;   // threads per fused rod-force CTA (kRodChunk - 1 nodes each)
+constexpr int kWNodes = 8;       // nodes per CTA of the warp-cooperative force kernel
+// Largest batch (nodes) given the warp-cooperative force kernel: below it the kernel's many
+// short float64 paths beat one long path per thread; above it every scheduler already has a
+// thread-per-segment warp and the duplicated per-lane work costs more than it saves.
+constexpr int kWarpForceMaxNodes = 4096;
 
 cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double* D, double t_off,
                               double* g64, double* m64, float* Xf, float* gf, float* mf,
@@ -60,10 +69,13 @@ cudaError_t launch_segment_table(int N, const int2* node_info, double wave_k, do
 // L.dt of every instance of the batch in one launch, then the step counter advances by nsteps.
 // Usable when the instance fits shared memory (fused_fits) -- float32 pair sum.
 constexpr size_t kFusedMaxSmem = 200 * 1024;
-// Largest instance the fused path takes by default.  Measured on GB300 (us per Euler step of a
-// single instance, fused / graphs): 51 nodes 16.2 / 21.4, 128 nodes 22.6 / 22.7, 192 nodes
-// 39.0 / 22.6, 512 nodes 163 / 26.5; 64-slice Parareal batches tie at 128 nodes and favour the
-// graphs from 192 on (3.6x at 512): one SM per instance stops paying beyond ~128 nodes.
+// Largest instance the fused path takes by default, for batches of more than
+// kWarpForceMaxNodes nodes.  Measured on GB300 (us per Euler step of a single instance, fused /
+// graphs with the thread-per-segment kernels): 51 nodes 16.2 / 21.4, 128 nodes 22.6 / 22.7,
+// 192 nodes 39.0 / 22.6, 512 nodes 163 / 26.5; 64-slice Parareal batches tie at 128 nodes and
+// favour the graphs from 192 on (3.6x at 512): one SM per instance stops paying beyond ~128
+// nodes.  With the warp-cooperative kernels (batches of up to kWarpForceMaxNodes nodes) the
+// graphs win outright: 51 nodes 15.6 / 11.6 us.
 constexpr int kFusedAutoNodes = 128;
 size_t fused_smem_bytes(int N1);
 bool fused_fits(int N1);
@@ -87,6 +99,8 @@ struct RodWorkspace {
     int2* d_node_info = nullptr;
     int* d_chunks = nullptr;
     int n_chunks = 0;
+    int* d_wchunks = nullptr;
+    int n_wchunks = 0;
     double* d_t0 = nullptr;
     long long* d_step = nullptr;
     double* d_FN = nullptr;
@@ -112,6 +126,7 @@ struct RodWorkspace {
         int steps;
         double dt;
         mrs_rod_params p;
+        int force_kernel;   // the context's rod force kernel setting at capture
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;

@@ -323,6 +323,244 @@ __global__ void __launch_bounds__(kRodChunk) rod_forces_fused_kernel(
             g64, m64, Xf, gf, mf, centred ? sref : nullptr);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Warp-cooperative force kernel for small systems.  The float64 pipe executes one warp
+// instruction in about 64 cycles per scheduler whatever the active mask, so a segment computed
+// by one thread costs its ~190 float64 instructions on one scheduler, and a rod of a few
+// hundred nodes keeps only a few dozen of the GPU's 608 schedulers busy.  Here the lanes of a
+// warp share the arithmetic of a segment instead: a CTA covers kWNodes consecutive nodes of one
+// rod (the kWNodes + 1 segments around them; chunks overlap by one segment) with four warps.
+//   * warps 0..2: three segments each, ten lanes per segment (lanes 30, 31 idle).  Nine lanes
+//     form A = D_{k+1} D_k^T (one entry each), the quaternion of A and the half-angle quaternion
+//     are formed redundantly by every lane (the same instructions, no extra cost), nine lanes
+//     form the rotation S and the mid frame Dh = S D_k, six lanes the three force and three
+//     moment coefficients and then the six components of F and N (Eqs. mid_triad,
+//     F_comp_discrete, N_comp_discrete; the same expressions as segment_core);
+//   * warp 3: the preferred curvature Omega_2 of every segment (one lane each, in parallel with
+//     the segment warps), the pack reference point, and after the segments the node force and
+//     torque of the CTA's nodes (three lanes per node, one per component; node_fn's terms).
+// The longest float64 path of a CTA is then about 70 instructions instead of ~230.
+// ---------------------------------------------------------------------------------------------
+constexpr int kWSegLanes = 10;   // lanes per segment in a segment warp
+constexpr int kWSegPerWarp = 3;  // segments per segment warp
+constexpr int kWSegs = kWNodes + 1;
+static_assert(kWSegs == 3 * kWSegPerWarp, "three segment warps cover a chunk's segments");
+static_assert(3 * kWNodes <= 32, "one lane per node component in the node phase");
+
+struct WSeg {          // per-segment shared scratch of rod_forces_warp_kernel
+    double A[9];       // D_{k+1} D_k^T
+    double S[9];       // its principal square root
+    double Dh[9];      // mid frame S D_k
+    double c[6];       // F_i (0..2), N_i (3..5)
+    double FN[6];      // F (lab), N (lab)
+    double om2;        // Omega_2 at the segment midpoint
+};
+
+// x with its sign flipped when neg (an exact operation, kept off the float64 pipe)
+__device__ __forceinline__ double flip_if(double x, bool neg)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+}
+
+__device__ __forceinline__ double sel4(int i, double a, double b, double c, double d)
+{
+    return i == 0 ? a : i == 1 ? b : i == 2 ? c : d;
+}
+
+// Segment warps, first part: A (nine lanes), its quaternion and the half-angle quaternion (every
+// lane of the group: rot_to_quat and rot_sqrt_dev without branches, so that the three groups of
+// a warp, which may take different branches, run one instruction stream), S (nine lanes) and
+// Dh = S D_k (nine lanes).
+__device__ __forceinline__ void wseg_frame(const double* __restrict__ Dk, bool valid, int sl, WSeg& W)
+{
+    const double* Dk1 = Dk + 9;
+    if (valid && sl < 9) {
+        const int r = sl / 3, c = sl - 3 * (sl / 3);
+        W.A[sl] = Dk1[r] * Dk[c] + Dk1[3 + r] * Dk[3 + c] + Dk1[6 + r] * Dk[6 + c];
+    }
+    __syncwarp();
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+    if (valid) {
+        double A[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) A[q] = W.A[q];
+        const double tr = A[0] + A[4] + A[8];
+        const int br = (tr >= A[0] && tr >= A[4] && tr >= A[8]) ? 0
+                       : (A[0] >= A[4] && A[0] >= A[8]) ? 1
+                       : (A[4] >= A[8]) ? 2 : 3;
+        // x of the branch: 1 + tr, or 1 +- A0 +- A4 +- A8 with + on the branch's own entry
+        const double u1 = br == 0 ? tr : flip_if(A[0], br != 1);
+        const double u2 = br == 0 ? 0.0 : flip_if(A[4], br != 2);
+        const double u3 = br == 0 ? 0.0 : flip_if(A[8], br != 3);
+        const double x = fmax(((1.0 + u1) + u2) + u3, 0.0), ir = rsqrt(x);
+        const double s = 0.5 * ir;
+        double q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            // component j: x s on the branch's own component, else (A[p] +- A[m]) s, the pair
+            // depending on {br, j} only
+            const int key = br < j ? 4 * br + j : 4 * j + br;
+            const double P = j == br ? x
+                             : key == 1 ? A[7] : key == 2 ? A[2] : key == 3 ? A[3]
+                             : key == 6 ? A[1] : key == 7 ? A[2] : A[5];
+            const double M = j == br ? 0.0
+                             : key == 1 ? -A[5] : key == 2 ? -A[6] : key == 3 ? -A[1]
+                             : key == 6 ? A[3] : key == 7 ? A[6] : A[7];
+            q[j] = (P + M) * s;
+        }
+        const bool ng = q[0] < 0.0;   // w >= 0
+        const double q0 = flip_if(q[0], ng), q1 = flip_if(q[1], ng), q2 = flip_if(q[2], ng),
+                     q3 = flip_if(q[3], ng);
+        const double w1 = 1.0 + q0;
+        const double inv = rsqrt(w1 * w1 + q1 * q1 + q2 * q2 + q3 * q3);
+        a = w1 * inv;
+        b = q1 * inv;
+        c = q2 * inv;
+        d = q3 * inv;
+    }
+    if (valid && sl < 9) {
+        // S[e] = alpha + beta (x1 y1 +- x2 y2) with (x1, y1, x2, y2) from (a, b, c, d):
+        //   e:  0     1     2     3     4     5     6     7     8
+        //      cc+dd bc-ad bd+ac bc+ad bb+dd cd-ab bd-ac cd+ab bb+cc
+        // alpha = 1, beta = -2 on the diagonal, alpha = 0, beta = 2 off it (2-bit fields by e)
+        const int e = sl;
+        const double x1 = sel4((0x19956 >> (2 * e)) & 3, a, b, c, d);
+        const double y1 = sel4((0x1fdba >> (2 * e)) & 3, a, b, c, d);
+        const double x2 = sel4((0x20303 >> (2 * e)) & 3, a, b, c, d);
+        const double y2 = sel4((0x267ef >> (2 * e)) & 3, a, b, c, d);
+        const bool diag = e == 0 || e == 4 || e == 8;
+        const double t = fma(x1, y1, flip_if(x2 * y2, (0x62 >> e) & 1));
+        W.S[e] = fma(diag ? -2.0 : 2.0, t, diag ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    if (valid && sl < 9) {
+        const int i = sl / 3, r = sl - 3 * (sl / 3);
+        W.Dh[sl] = W.S[3 * r] * Dk[3 * i] + W.S[3 * r + 1] * Dk[3 * i + 1] + W.S[3 * r + 2] * Dk[3 * i + 2];
+    }
+    __syncwarp();
+}
+
+// Segment warps, second part (after Omega_2 is known): the coefficients F_i = b_i (e.Dh_i -
+// delta_i3), N_i = a_i ((d_j(k+1) - d_j(k)).Dh_l / ds - delta_i2 Omega_2) (six lanes, one
+// instruction stream: u = P - Q scaled before or after the dot product), then F = sum F_i Dh_i
+// and N = sum N_i Dh_i (six lanes, one component each).
+__device__ __forceinline__ void wseg_forces(const mrs_rod_params& P, const double* __restrict__ Xk,
+                                            const double* __restrict__ Dk, double ids, bool valid,
+                                            int sl, WSeg& W)
+{
+    if (valid && sl < 6) {
+        const int i = sl % 3;
+        const bool isN = sl >= 3;
+        const int jd = (i + 1) % 3, l = (i + 2) % 3;
+        const double* Pp = isN ? Dk + 9 + 3 * jd : Xk + 3;
+        const double* Qp = isN ? Dk + 3 * jd : Xk;
+        const double sc1 = isN ? 1.0 : ids, sc2 = isN ? ids : 1.0;
+        const double* w = W.Dh + 3 * (isN ? l : i);
+        const double u0 = (Pp[0] - Qp[0]) * sc1, u1 = (Pp[1] - Qp[1]) * sc1, u2 = (Pp[2] - Qp[2]) * sc1;
+        const double dotv = u0 * w[0] + u1 * w[1] + u2 * w[2];
+        const double coef = isN ? P.a[i] : P.b[i];
+        const double off = isN ? (i == 1 ? W.om2 : 0.0) : (i == 2 ? 1.0 : 0.0);
+        W.c[sl] = coef * (dotv * sc2 - off);
+    }
+    __syncwarp();
+    if (valid && sl < 6) {
+        const int cc = sl % 3;
+        const double* cf = W.c + (sl >= 3 ? 3 : 0);
+        W.FN[sl] = fma(cf[2], W.Dh[6 + cc], fma(cf[1], W.Dh[3 + cc], cf[0] * W.Dh[cc]));
+    }
+}
+
+__global__ void __launch_bounds__(128) rod_forces_warp_kernel(
+    const RodLaunch L, const double* __restrict__ X, const double* __restrict__ D, double t_off,
+    double* g64, double* m64, float* Xf, float* gf, float* mf)
+{
+    pdl_wait();
+    __shared__ WSeg sW[kWSegs];
+    __shared__ double sref[3];
+    const long long k0 = L.wchunks[blockIdx.x];
+#if MRS_DEBUG_BOUNDS
+    if (k0 < 0 || k0 >= L.N) {   // every thread reads the same chunk: the CTA leaves together
+        if (threadIdx.x == 0 && L.err) atomicOr(L.err, MRS_FLAG_BOUNDS);
+        return;
+    }
+#endif
+    const int2 ni0 = L.node_info[k0];
+    if (!node_checked(L, ni0, k0, L.N)) return;   // the same entry for every thread of the CTA
+    const int M = ni0.y, b0 = ni0.x;              // the rod's nodes, the chunk's first node in it
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int inst = (int)(k0 / L.nodes_per_inst);
+    const double ids = (double)(M - 1) * L.inv_L;
+    const bool centred = Xf && L.n_ref > 0;
+
+    // segment s of the chunk is segment b0 - 1 + s of the rod (nodes k0 - 1 + s and k0 + s)
+    const int g = lane / kWSegLanes, sl = lane - kWSegLanes * g;
+    const int s = kWSegPerWarp * warp + g;
+    const bool seg_valid = warp < 3 && g < kWSegPerWarp && b0 - 1 + s >= 0 && b0 - 1 + s < M - 1;
+    const long long ks = k0 - 1 + s;
+    const double* Xk = X + 3 * (seg_valid ? ks : k0);
+    const double* Dk = D + 9 * (seg_valid ? ks : k0);
+
+    if (warp < 3) {
+        wseg_frame(Dk, seg_valid, sl, sW[g < kWSegPerWarp ? s : 0]);
+    } else if (lane < kWSegs && b0 - 1 + lane >= 0 && b0 - 1 + lane < M - 1) {
+        // Omega_2 of segment `lane` (segment_fn's two forms)
+        const double amp = -L.p.wave_k * L.p.wave_k * L.p.wave_A;
+        const double t = L.t0[inst] + (double)(*L.step) * L.dt + t_off;
+        double om2;
+        if (L.segsc) {
+            double sft, cft;
+            sincos(L.p.wave_f * t, &sft, &cft);
+            const double2 v = L.segsc[k0 - 1 + lane];
+            om2 = amp * (v.x * cft + v.y * sft);
+        } else {
+            const double s_mid = ((double)(b0 - 1 + lane) + 0.5) * (L.p.L / (double)(M - 1));
+            om2 = amp * sin(L.p.wave_k * s_mid + L.p.wave_f * t);
+        }
+        sW[lane].om2 = om2;
+    }
+    __syncthreads();
+    if (warp < 3) {
+        wseg_forces(L.p, Xk, Dk, ids, seg_valid, sl, sW[g < kWSegPerWarp ? s : 0]);
+    } else if (centred && lane < 3) {
+        // pack_reference, component `lane`, summed in the same order
+        const double* Xi = X + 3 * (size_t)inst * L.nodes_per_inst;
+        double acc = 0.0;
+        for (int i = 0; i < L.n_ref; ++i) acc += Xi[3 * L.ref[i] + lane];
+        sref[lane] = acc * L.ref_w;
+    }
+    __syncthreads();
+    if (warp != 3 || lane >= 3 * kWNodes) return;
+    // node phase: node nn of the chunk, component c (node_fn's terms)
+    const int nn = lane / 3, c = lane - 3 * (lane / 3);
+    const int nb = b0 + nn;
+    if (nb >= M) return;
+    const long long k = k0 + nn;
+    const double* Xn = X + 3 * (size_t)k;
+    const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+    double gv = 0.0, mv = 0.0;
+    if (nb < M - 1) {   // segment k+1/2 = chunk segment nn + 1
+        const double* fp = sW[nn + 1].FN;
+        const double dX1 = Xn[3 + c1] - Xn[c1], dX2 = Xn[3 + c2] - Xn[c2];
+        gv += fp[c];
+        mv += fp[3 + c] + 0.5 * (dX1 * fp[c2] - dX2 * fp[c1]);
+    }
+    if (nb > 0) {       // segment k-1/2 = chunk segment nn
+        const double* fm = sW[nn].FN;
+        const double dX1 = Xn[c1] - Xn[c1 - 3], dX2 = Xn[c2] - Xn[c2 - 3];
+        gv -= fm[c];
+        mv += -fm[3 + c] + 0.5 * (dX1 * fm[c2] - dX2 * fm[c1]);
+    }
+    if (g64) {
+        g64[3 * (size_t)k + c] = gv;
+        m64[3 * (size_t)k + c] = mv;
+    }
+    if (Xf) {
+        Xf[3 * (size_t)k + c] = (float)(centred ? Xn[c] - sref[c] : Xn[c]);
+        gf[3 * (size_t)k + c] = (float)gv;
+        mf[3 * (size_t)k + c] = (float)mv;
+    }
+}
+
 // Eq. (newD): rotate the three directors of node k by |w| h about w / |w| (unchanged if w = 0),
 // written without normalising w: with theta^2 = |w|^2 h^2,
 //   D' = cos(theta) D + (sin(theta)/theta) h (w x D) + ((1 - cos(theta))/theta^2) h^2 (w.D) w,
@@ -386,6 +624,70 @@ __global__ void rod_update_kernel(const RodLaunch L, const double* X0, const dou
     for (int c = 0; c < 3; ++c) X1[3 * (size_t)k + c] = X0[3 * (size_t)k + c] + (double)u[3 * (size_t)k + c] * h;
 #pragma unroll
     for (int q = 0; q < 9; ++q) D1[9 * (size_t)k + q] = Dn[q];
+}
+
+// Warp-cooperative update for small systems (same float64-pipe argument as
+// rod_forces_warp_kernel): nine lanes per node, one entry (director i, component c) of the new
+// frame each, three nodes per warp.  Every lane of a node forms rodrigues' coefficients (the
+// same instructions, no extra cost); a lane then needs only its director's projection on w and
+// one component of w x d_i.  Each lane loads everything it reads before any lane of the warp
+// stores, so X1/D1 may alias X0/D0.  When bump_step is set, lane 0 of node 0 advances the step
+// counter.
+constexpr int kUNodesPerWarp = 3;   // nine lanes each; lanes 27..31 idle
+
+template <typename VT>
+__global__ void __launch_bounds__(128) rod_update_warp_kernel(const RodLaunch L, const double* X0,
+                                                              const double* D0, const VT* __restrict__ u,
+                                                              const VT* __restrict__ w, double h,
+                                                              double* X1, double* D1, int bump_step)
+{
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int sub = lane / 9, e = lane - 9 * (lane / 9);
+    const long long k = gw * kUNodesPerWarp + sub;
+    const bool active = sub < kUNodesPerWarp && k < L.N;
+    if (bump_step && k == 0 && e == 0) *L.step += 1;
+    const int i = e / 3, c = e - 3 * (e / 3);
+    double d1 = 0.0, x1 = 0.0;
+    if (active) {
+        const double wx = (double)w[3 * k], wy = (double)w[3 * k + 1], wz = (double)w[3 * k + 2];
+        const double* v = D0 + 9 * k + 3 * i;
+        const double v0 = v[0], v1 = v[1], v2 = v[2];
+        const double vc = c == 0 ? v0 : c == 1 ? v1 : v2;
+        const double w2 = wx * wx + wy * wy + wz * wz;
+        if (w2 == 0.0) {
+            d1 = vc;
+        } else {
+            const double q = w2 * h * h;   // theta^2 (rodrigues' two forms of the ratios)
+            double ct, sc, cc;
+            if (q < 1e-3) {
+                sc = 1.0 + q * (-1.0 / 6.0 + q * (1.0 / 120.0 + q * (-1.0 / 5040.0 + q * (1.0 / 362880.0))));
+                cc = 0.5 + q * (-1.0 / 24.0 + q * (1.0 / 720.0 + q * (-1.0 / 40320.0 + q * (1.0 / 3628800.0))));
+                ct = 1.0 - q * cc;
+            } else {
+                const double th = sqrt(q);
+                double st;
+                sincos(th, &st, &ct);
+                sc = st / th;
+                cc = (1.0 - ct) / q;
+            }
+            const double a = sc * h, b = cc * h * h;
+            const double wv = b * (wx * v0 + wy * v1 + wz * v2);
+            // component c of w x d_i = wA vB - wB vA: (wy v2 - wz v1, wz v0 - wx v2, wx v1 - wy v0)
+            const double wA = c == 0 ? wy : c == 1 ? wz : wx, vB = c == 0 ? v2 : c == 1 ? v0 : v1;
+            const double wB = c == 0 ? wz : c == 1 ? wx : wy, vA = c == 0 ? v1 : c == 1 ? v2 : v0;
+            const double cr = wA * vB - wB * vA;
+            const double wc = c == 0 ? wx : c == 1 ? wy : wz;
+            d1 = ct * vc + a * cr + wv * wc;
+        }
+        if (e < 3) x1 = X0[3 * k + e] + (double)u[3 * k + e] * h;
+    }
+    __syncwarp();   // every lane of the warp has read X0/D0 before any lane stores
+    if (active) {
+        D1[9 * k + e] = d1;
+        if (e < 3) X1[3 * k + e] = x1;
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -779,7 +1081,11 @@ cudaError_t launch_rod_forces(const RodLaunch& L, const double* X, const double*
                               cudaStream_t s)
 {
     if (L.N == 0) return cudaSuccess;
-    if (L.chunks != nullptr) {
+    if (L.wchunks != nullptr) {
+        cudaError_t e = launch_pdl(rod_forces_warp_kernel, dim3(L.n_wchunks), dim3(128), 0, s, L, X, D, t_off,
+                                   g64, m64, Xf, gf, mf);
+        if (e != cudaSuccess) return e;
+    } else if (L.chunks != nullptr) {
         cudaError_t e = launch_pdl(rod_forces_fused_kernel, dim3(L.n_chunks), dim3(kRodChunk), 0, s,
                                    L, X, D, t_off, g64, m64, Xf, gf, mf);
         if (e != cudaSuccess) return e;
@@ -801,6 +1107,9 @@ cudaError_t launch_rod_update(const RodLaunch& L, const double* X0, const double
                               bool bump_step, cudaStream_t s)
 {
     if (L.N == 0) return cudaSuccess;
+    if (L.wchunks != nullptr)   // small batch: warp-cooperative (see rod_forces_warp_kernel)
+        return launch_pdl(rod_update_warp_kernel<float>, dim3(nblk(L.N, 4 * kUNodesPerWarp)), dim3(128), 0, s,
+                          L, X0, D0, u, w, h, X1, D1, bump_step ? 1 : 0);
     return launch_pdl(rod_update_kernel<float>, dim3(nblk(L.N, 128)), dim3(128), 0, s, L, X0, D0, u, w,
                       h, X1, D1, bump_step ? 1 : 0);
 }
@@ -810,6 +1119,9 @@ cudaError_t launch_rod_update64(const RodLaunch& L, const double* X0, const doub
                                 double* D1, bool bump_step, cudaStream_t s)
 {
     if (L.N == 0) return cudaSuccess;
+    if (L.wchunks != nullptr)
+        return launch_pdl(rod_update_warp_kernel<double>, dim3(nblk(L.N, 4 * kUNodesPerWarp)), dim3(128), 0,
+                          s, L, X0, D0, u, w, h, X1, D1, bump_step ? 1 : 0);
     return launch_pdl(rod_update_kernel<double>, dim3(nblk(L.N, 128)), dim3(128), 0, s, L, X0, D0, u,
                       w, h, X1, D1, bump_step ? 1 : 0);
 }

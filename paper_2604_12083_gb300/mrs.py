@@ -30,7 +30,8 @@ STATUS_NAMES = {0: "MRS_OK", 1: "MRS_EINVAL", 2: "MRS_ENOMEM", 3: "MRS_ECUDA", 4
 # Every symbol include/mrs_gb300.h declares (kept in sync by tests/test_abi.py).
 EXPORTS = [
     "mrs_last_error", "mrs_version", "mrs_ctx_create", "mrs_ctx_destroy", "mrs_ctx_num_sms",
-    "mrs_ctx_set_fused_steps", "mrs_ctx_set_sym_pass_bytes", "mrs_fma_probe",
+    "mrs_ctx_set_fused_steps", "mrs_ctx_set_rod_force_kernel", "mrs_ctx_set_sym_pass_bytes",
+    "mrs_fma_probe",
     "mrs_velocity", "mrs_plan_create", "mrs_plan_execute", "mrs_plan_destroy",
     "mrs_plan_config_count", "mrs_plan_config_symmetric", "mrs_plan_config_info", "mrs_plan_info",
     "mrs_plan_scratch",
@@ -115,6 +116,7 @@ def lib():
         L.mrs_ctx_destroy.argtypes = [_vp]
         L.mrs_ctx_num_sms.argtypes = [_vp]
         L.mrs_ctx_set_fused_steps.argtypes = [_vp, ctypes.c_int]
+        L.mrs_ctx_set_rod_force_kernel.argtypes = [_vp, ctypes.c_int]
         L.mrs_ctx_set_sym_pass_bytes.argtypes = [_vp, ctypes.c_size_t]
         L.mrs_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
                                     ctypes.POINTER(ctypes.c_float)]
@@ -213,8 +215,15 @@ class Context:
 
     def set_fused_steps(self, mode: int) -> None:
         """``mrs_ctx_set_fused_steps``: 1 (default) one fused launch per rod-stepping call for
-        instances of at most 128 nodes, 2 whenever the instance fits shared memory, 0 never."""
+        instances of at most 128 nodes in batches of more than 4096 nodes, 2 whenever the
+        instance fits shared memory, 0 never."""
         _check(lib().mrs_ctx_set_fused_steps(self.handle, int(mode)))
+
+    def set_rod_force_kernel(self, mode: int) -> None:
+        """``mrs_ctx_set_rod_force_kernel``: 0 (default) warp-cooperative force kernel for
+        batches of at most 4096 nodes, 1 always one thread per segment, 2 always
+        warp-cooperative."""
+        _check(lib().mrs_ctx_set_rod_force_kernel(self.handle, int(mode)))
 
     def device_status(self) -> int:
         """``mrs_device_status``: anomaly flags since the last call (synchronizes, clears)."""

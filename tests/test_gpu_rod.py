@@ -107,6 +107,72 @@ def test_rod_forces_match_oracle(ctx, orc):
         assert np.abs(mm - mo).max() <= 1e-11 * np.abs(mo).max()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_rod_force_kernels_match_oracle(ctx, orc, mode):
+    """Both force kernels -- one thread per segment (mode 1) and warp-cooperative (mode 2) -- on
+    rods of 2, 3, 8, 9, 16, 17, 51 and 300 nodes (around the warp kernel's chunks of 8 nodes
+    and the thread kernel's of 127), once with frames near their neighbours' (the quaternion
+    branch of the trace) and once with independent random frames (relative rotations of any
+    angle below pi: every branch of the rotation square root), at two times: against the
+    oracle to 1e-11 of the largest entry."""
+    from scipy.spatial.transform import Rotation
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    sizes = [2, 3, 8, 9, 16, 17, 51, 300]
+    rng = np.random.default_rng(91)
+    Xs, Ds = [], []
+    for M in sizes:
+        X, D = W.sinusoid_filament(M)
+        Xs.append(X + rng.uniform(0.0, 2.0, 3))
+        Ds.append(D)
+    X = np.concatenate(Xs)
+    D0 = np.concatenate(Ds)
+    Drand = Rotation.random(len(X), random_state=92).as_matrix()   # rows: the directors
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    gp, op = params(dict(W.ROD_PLAIN), 0.01)
+    ctx.set_rod_force_kernel(mode)
+    try:
+        for D in (D0, Drand):
+            for t in (0.0, 0.37):
+                Xd, Dd = torch.from_numpy(X).cuda(), torch.from_numpy(D).cuda()
+                g, m = torch.empty_like(Xd), torch.empty_like(Xd)
+                mrs.rod_forces(ctx, off, gp, Xd, Dd, t, g, m)
+                torch.cuda.synchronize()
+                go, mo = orc.rod_forces(off, X, D, op, t)
+                gg, mm = g.cpu().numpy(), m.cpu().numpy()
+                assert np.abs(gg - go).max() <= 1e-11 * np.abs(go).max(), (mode, t)
+                assert np.abs(mm - mo).max() <= 1e-11 * np.abs(mo).max(), (mode, t)
+    finally:
+        ctx.set_rod_force_kernel(0)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_rod_force_kernels_agree_in_stepping(ctx, orc, scheme):
+    """200 steps of 4 rods of 51 points (a paper size) on the kernel graphs with each force
+    kernel: both match the oracle's steps (float32 pair sum: 1e-4 on the displacement) and each
+    other to float32 rounding of the packed forces."""
+    from paper_2604_12083_gb300 import mrs, workloads as W
+    rs, X, D = perturbed(93, 4, 51)
+    cfg = dict(W.ROD_PLAIN)
+    eps = 4.0 / 50
+    gp, op = params(cfg, eps)
+    dt = cfg["dt"]
+    Xo, _ = orc.rod_step(rs.rod_off, X, D, op, eps, 1.0, 0.0, dt, 200, scheme)
+    out = {}
+    try:
+        ctx.set_fused_steps(0)
+        for mode in (1, 2):
+            ctx.set_rod_force_kernel(mode)
+            Xs_, Ds_ = torch.from_numpy(X.copy()).cuda(), torch.from_numpy(D.copy()).cuda()
+            mrs.rod_step(ctx, rs.rod_off, gp, Xs_, Ds_, 0.0, dt, 200, scheme)
+            torch.cuda.synchronize()
+            out[mode] = Xs_.cpu().numpy()
+            assert rel(out[mode] - X, Xo - X) < 1e-4, mode
+    finally:
+        ctx.set_rod_force_kernel(0)
+        ctx.set_fused_steps(1)
+    assert rel(out[2] - X, out[1] - X) < 1e-6
+
+
 @pytest.mark.parametrize("scheme", [0, 1])
 def test_plain_rod_200_steps(ctx, orc, scheme):
     """One rod of 128 nodes, 200 steps at dt = 1e-6 (the plain-method configuration)."""
@@ -332,7 +398,7 @@ def test_parareal_reports_non_convergence(ctx):
 @pytest.mark.parametrize("scheme", [0, 1])
 def test_fused_and_graph_stepping_agree(ctx, orc, scheme):
     """The fused path (one launch per call, state in shared memory; the default for small
-    instances) and the per-step kernel graphs compute the same steps: 200 steps of the
+    instances in large batches) and the per-step kernel graphs compute the same steps: 200 steps of the
     128-node rod and of four interacting 64-node rods agree to float32 rounding of the pair
     sum, and both match the oracle."""
     from paper_2604_12083_gb300 import mrs, workloads as W
