@@ -380,8 +380,9 @@ static bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb)
 }
 
 int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const void* Xt, void* u,
-             void* w, cudaStream_t s)
+             void* w, cudaStream_t s, const PlanUpdate* up, bool* fused)
 {
+    if (fused) *fused = false;
     MRS_REQUIRE(p != nullptr, "plan is NULL");
     if (p->n_points == 0) return MRS_OK;
     MRS_REQUIRE(X && f && n && u && w, "NULL input or output pointer");
@@ -468,6 +469,15 @@ int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const voi
                 if (e != cudaSuccess) break;
             }
         } else {
+            if (up && p->cl > 0) {   // the cluster kernel applies the rod-step update itself
+                L.upX0 = up->X0;
+                L.upD0 = up->D0;
+                L.upX1 = up->X1;
+                L.upD1 = up->D1;
+                L.up_h = up->h;
+                L.up_step = up->step;
+                if (fused) *fused = true;
+            }
             e = launch_mrs_f32(p->ocfg, p->precision == MRS_F32_COMP, L, s);
         }
     }

@@ -180,6 +180,16 @@ struct MrsLaunch {
     long long n_points;   // points of the arrays (index checks of the debug build)
     unsigned int* err;    // device error word: bit 0 = a non-finite output was written
     int cl = 0;           // cluster kernel: CTAs per cluster (P = n_tiles * cl); else unused
+    // Rod stepping (cluster kernel only): when upX0 is set, the CTA that completes a target
+    // also applies the update of Eqs. (newx, newD) to it with the velocities just summed:
+    // X1 = X0 + u h, D1 = the frame D0 rotated by |w| h about w (float64; X1/D1 may alias
+    // X0/D0, which the pair sum itself never reads); up_step (or NULL) advances by one.
+    const double* upX0 = nullptr;
+    const double* upD0 = nullptr;
+    double* upX1 = nullptr;
+    double* upD1 = nullptr;
+    double up_h = 0.0;
+    long long* up_step = nullptr;
 };
 
 cudaError_t launch_mrs_f32(int config, bool comp, const MrsLaunch& L, cudaStream_t s);
@@ -379,8 +389,20 @@ struct mrs_ctx {
 namespace mrs {
 int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
                const double* eps_per_sys, int precision, int config, mrs_plan** out);
+// Rod-step update applied by the pair sum itself (MrsLaunch::upX0 ...), when the plan runs the
+// cluster kernel.
+struct PlanUpdate {
+    const double* X0;
+    const double* D0;
+    double* X1;
+    double* D1;
+    double h;
+    long long* step;   // advanced by one, or NULL
+};
+// up != NULL: apply *up in the pair-sum launch when the plan allows it; *fused (when given)
+// tells whether it did (otherwise the caller runs the update itself).
 int plan_run(mrs_plan* p, const void* X, const void* f, const void* n, const void* Xt, void* u,
-             void* w, cudaStream_t s);
+             void* w, cudaStream_t s, const PlanUpdate* up = nullptr, bool* fused = nullptr);
 void plan_free(mrs_plan* p);
 int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precision);
 int default_ordered_config(int n_sys, const int64_t* offsets);

@@ -35,6 +35,7 @@
 #include "mrs_device.cuh"
 #include "mrs_checks.h"
 #include "mrs_internal.h"
+#include "rod_update.cuh"
 
 namespace mrs {
 
@@ -503,6 +504,7 @@ __global__ void __launch_bounds__(TM * G) mrs_f32_cluster(const MrsLaunch L)
     __shared__ __align__(16) float sflat[kChunk * 9];
     __shared__ float sgrp[G > 1 ? G * 6 * TM : 1];   // each group's partial: [group][component][target]
     __shared__ float spart[6 * TM];                  // the CTA's partial: [component][target]
+    __shared__ float sv[6 * TM];                     // completed velocities (update epilogue)
 
     const int tid = threadIdx.x;
     const int lt = tid % TM, g = tid / TM;   // target of the tile, source group
@@ -615,6 +617,35 @@ __global__ void __launch_bounds__(TM * G) mrs_f32_cluster(const MrsLaunch L)
             const float val = __fsub_rn(tot, cmp) * sc.scale;
             if (!isfinite(val)) atomicOr(L.err, 1u);
             if (q < 3) L.u[gi * 3 + q] = val; else L.w[gi * 3 + q - 3] = val;
+            sv[(li - lo) * 6 + q] = val;
+        }
+    }
+
+    if (L.upX0) {
+        // update epilogue: nine threads per completed target, one entry (director i, component
+        // c) of its new frame each, the first three also one position component; every thread
+        // reads what it needs before any thread of the CTA stores (in-place update)
+        if (L.up_step && blockIdx.x == 0 && tid == 0) *L.up_step += 1;
+        const int nloc = ok ? max(0, min(hi, T.tn) - lo) : 0;
+        __syncthreads();   // sv complete
+        for (int base = 0; base < nloc * 9; base += BLOCK) {
+            const int idx = base + tid;
+            const bool act = idx < nloc * 9;
+            const int nl = idx / 9, e = idx - 9 * (idx / 9);
+            const long long gk = (long long)T.t0 + lo + (act ? nl : 0);
+            double d1 = 0.0, x1 = 0.0;
+            if (act) {
+                const int i = e / 3, c = e - 3 * (e / 3);
+                const float* vv = sv + nl * 6;
+                const double* v = L.upD0 + 9 * gk + 3 * i;
+                d1 = rodrigues_entry(v[0], v[1], v[2], (double)vv[3], (double)vv[4], (double)vv[5], L.up_h, c);
+                if (e < 3) x1 = L.upX0[3 * gk + e] + (double)vv[e] * L.up_h;
+            }
+            __syncthreads();
+            if (act) {
+                L.upD1[9 * gk + e] = d1;
+                if (e < 3) L.upX1[3 * gk + e] = x1;
+            }
         }
     }
 

@@ -208,10 +208,14 @@ int rod_ws_set_times(RodWorkspace* ws, double t_first, double dT, cudaStream_t s
     return MRS_OK;
 }
 
-// Velocities of the current stage: forces -> (float32 pack) -> pair sum.
+// Velocities of the current stage: forces -> (float32 pack) -> pair sum.  up (or NULL): the
+// update that follows, which the pair sum applies itself when its plan runs the cluster kernel
+// (*fused then true).
 static int enqueue_velocity(RodWorkspace* ws, const RodLaunch& L, const double* X, const double* D,
-                            double t_off, cudaStream_t s)
+                            double t_off, cudaStream_t s, const PlanUpdate* up = nullptr,
+                            bool* fused = nullptr)
 {
+    if (fused) *fused = false;
     cudaError_t e;
     if (ws->precision == MRS_F64) {
         e = launch_rod_forces(L, X, D, t_off, ws->d_g64, ws->d_m64, nullptr, nullptr, nullptr, s);
@@ -226,7 +230,7 @@ static int enqueue_velocity(RodWorkspace* ws, const RodLaunch& L, const double* 
         set_error("rod force kernels failed: %s", cudaGetErrorString(e));
         return MRS_ECUDA;
     }
-    return plan_run(ws->plan, ws->d_Xf, ws->d_gf, ws->d_mf, nullptr, ws->d_u, ws->d_w, s);
+    return plan_run(ws->plan, ws->d_Xf, ws->d_gf, ws->d_mf, nullptr, ws->d_u, ws->d_w, s, up, fused);
 }
 
 static cudaError_t enqueue_update(RodWorkspace* ws, const RodLaunch& L, const double* X0,
@@ -238,28 +242,35 @@ static cudaError_t enqueue_update(RodWorkspace* ws, const RodLaunch& L, const do
     return launch_rod_update(L, X0, D0, ws->d_u, ws->d_w, h, X1, D1, bump, s);
 }
 
-// One time step (Euler or explicit-midpoint RK2) enqueued on s.
-static int enqueue_step(RodWorkspace* ws, const RodLaunch& L, double* X, double* D, int scheme,
-                        cudaStream_t s)
+// One stage: velocities at (Xs, Ds, t_off), then (X1, D1) = update of (X0, D0) by h with them
+// (in the pair-sum launch when its plan allows, else by the update kernel).
+static int enqueue_stage(RodWorkspace* ws, const RodLaunch& L, const double* Xs, const double* Ds,
+                         double t_off, const double* X0, const double* D0, double h, double* X1,
+                         double* D1, bool bump, cudaStream_t s)
 {
-    int st = enqueue_velocity(ws, L, X, D, 0.0, s);
-    if (st) return st;
-    cudaError_t e;
-    if (scheme == MRS_EULER) {
-        e = enqueue_update(ws, L, X, D, L.dt, X, D, true, s);
-    } else {
-        e = enqueue_update(ws, L, X, D, 0.5 * L.dt, ws->d_Xh, ws->d_Dh, false, s);
-        if (e == cudaSuccess) {
-            st = enqueue_velocity(ws, L, ws->d_Xh, ws->d_Dh, 0.5 * L.dt, s);
-            if (st) return st;
-            e = enqueue_update(ws, L, X, D, L.dt, X, D, true, s);
-        }
-    }
+    // with the warp-cooperative kernels (small batches, mrs_ctx_set_rod_force_kernel) only: the
+    // thread-per-segment setting keeps the separate update kernel
+    const PlanUpdate up{X0, D0, X1, D1, h, bump ? L.step : nullptr};
+    const bool offer = ws->precision != MRS_F64 && L.wchunks != nullptr;
+    bool fused = false;
+    int st = enqueue_velocity(ws, L, Xs, Ds, t_off, s, offer ? &up : nullptr, &fused);
+    if (st || fused) return st;
+    const cudaError_t e = enqueue_update(ws, L, X0, D0, h, X1, D1, bump, s);
     if (e != cudaSuccess) {
         set_error("rod update kernel failed: %s", cudaGetErrorString(e));
         return MRS_ECUDA;
     }
     return MRS_OK;
+}
+
+// One time step (Euler or explicit-midpoint RK2) enqueued on s.
+static int enqueue_step(RodWorkspace* ws, const RodLaunch& L, double* X, double* D, int scheme,
+                        cudaStream_t s)
+{
+    if (scheme == MRS_EULER) return enqueue_stage(ws, L, X, D, 0.0, X, D, L.dt, X, D, true, s);
+    const int st = enqueue_stage(ws, L, X, D, 0.0, X, D, 0.5 * L.dt, ws->d_Xh, ws->d_Dh, false, s);
+    if (st) return st;
+    return enqueue_stage(ws, L, ws->d_Xh, ws->d_Dh, 0.5 * L.dt, X, D, L.dt, X, D, true, s);
 }
 
 static int get_graph(RodWorkspace* ws, const mrs_rod_params* p, double* X, double* D, double dt,

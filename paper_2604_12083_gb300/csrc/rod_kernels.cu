@@ -18,6 +18,7 @@
 
 #include "mrs_checks.h"
 #include "rod_internal.h"
+#include "rod_update.cuh"
 
 namespace mrs {
 
@@ -628,9 +629,9 @@ __global__ void rod_update_kernel(const RodLaunch L, const double* X0, const dou
 
 // Warp-cooperative update for small systems (same float64-pipe argument as
 // rod_forces_warp_kernel): nine lanes per node, one entry (director i, component c) of the new
-// frame each, three nodes per warp.  Every lane of a node forms rodrigues' coefficients (the
-// same instructions, no extra cost); a lane then needs only its director's projection on w and
-// one component of w x d_i.  Each lane loads everything it reads before any lane of the warp
+// frame each (rodrigues_entry), three nodes per warp.  Every lane of a node forms Rodrigues'
+// coefficients (the same instructions, no extra cost); a lane then needs only its director's
+// projection on w and one component of w x d_i.  Each lane loads everything it reads before any lane of the warp
 // stores, so X1/D1 may alias X0/D0.  When bump_step is set, lane 0 of node 0 advances the step
 // counter.
 constexpr int kUNodesPerWarp = 3;   // nine lanes each; lanes 27..31 idle
@@ -651,36 +652,9 @@ __global__ void __launch_bounds__(128) rod_update_warp_kernel(const RodLaunch L,
     const int i = e / 3, c = e - 3 * (e / 3);
     double d1 = 0.0, x1 = 0.0;
     if (active) {
-        const double wx = (double)w[3 * k], wy = (double)w[3 * k + 1], wz = (double)w[3 * k + 2];
         const double* v = D0 + 9 * k + 3 * i;
-        const double v0 = v[0], v1 = v[1], v2 = v[2];
-        const double vc = c == 0 ? v0 : c == 1 ? v1 : v2;
-        const double w2 = wx * wx + wy * wy + wz * wz;
-        if (w2 == 0.0) {
-            d1 = vc;
-        } else {
-            const double q = w2 * h * h;   // theta^2 (rodrigues' two forms of the ratios)
-            double ct, sc, cc;
-            if (q < 1e-3) {
-                sc = 1.0 + q * (-1.0 / 6.0 + q * (1.0 / 120.0 + q * (-1.0 / 5040.0 + q * (1.0 / 362880.0))));
-                cc = 0.5 + q * (-1.0 / 24.0 + q * (1.0 / 720.0 + q * (-1.0 / 40320.0 + q * (1.0 / 3628800.0))));
-                ct = 1.0 - q * cc;
-            } else {
-                const double th = sqrt(q);
-                double st;
-                sincos(th, &st, &ct);
-                sc = st / th;
-                cc = (1.0 - ct) / q;
-            }
-            const double a = sc * h, b = cc * h * h;
-            const double wv = b * (wx * v0 + wy * v1 + wz * v2);
-            // component c of w x d_i = wA vB - wB vA: (wy v2 - wz v1, wz v0 - wx v2, wx v1 - wy v0)
-            const double wA = c == 0 ? wy : c == 1 ? wz : wx, vB = c == 0 ? v2 : c == 1 ? v0 : v1;
-            const double wB = c == 0 ? wz : c == 1 ? wx : wy, vA = c == 0 ? v1 : c == 1 ? v2 : v0;
-            const double cr = wA * vB - wB * vA;
-            const double wc = c == 0 ? wx : c == 1 ? wy : wz;
-            d1 = ct * vc + a * cr + wv * wc;
-        }
+        d1 = rodrigues_entry(v[0], v[1], v[2], (double)w[3 * k], (double)w[3 * k + 1], (double)w[3 * k + 2],
+                             h, c);
         if (e < 3) x1 = X0[3 * k + e] + (double)u[3 * k + e] * h;
     }
     __syncwarp();   // every lane of the warp has read X0/D0 before any lane stores
