@@ -94,14 +94,16 @@ int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int
     ws->N = ws->N1 * n_inst;
     const size_t N = (size_t)ws->N;
     std::vector<int2> info(N);
-    std::vector<int> chunks, wchunks;
+    std::vector<int> chunks;
+    std::vector<int4> wchunks;
     for (int i = 0; i < n_inst; ++i)
         for (int r = 0; r < n_rods; ++r) {
             const int M = (int)(rod_off[r + 1] - rod_off[r]);
             for (int k = 0; k < M; ++k) info[(size_t)i * ws->N1 + rod_off[r] + k] = make_int2(k, M);
             for (int c = 0; c < M; c += kRodChunk - 1)
                 chunks.push_back((int)((size_t)i * ws->N1 + rod_off[r] + c));
-            for (int c = 0; c < M; c += kWNodes) wchunks.push_back((int)((size_t)i * ws->N1 + rod_off[r] + c));
+            for (int c = 0; c < M; c += kWNodes)
+                wchunks.push_back(make_int4((int)((size_t)i * ws->N1 + rod_off[r] + c), M, c, i));
         }
     ws->n_chunks = (int)chunks.size();
     ws->n_wchunks = (int)wchunks.size();
@@ -132,7 +134,7 @@ int rod_ws_get(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, int n_inst, int
     cudaMemcpy(ws->d_node_info, info.data(), N * sizeof(int2), cudaMemcpyHostToDevice);
     cudaMemcpy(ws->d_chunks, chunks.data(), chunks.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (ws->n_wchunks)
-        cudaMemcpy(ws->d_wchunks, wchunks.data(), wchunks.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(ws->d_wchunks, wchunks.data(), wchunks.size() * sizeof(int4), cudaMemcpyHostToDevice);
     cudaMemset(ws->d_t0, 0, n_inst * sizeof(double));
     cudaMemset(ws->d_step, 0, sizeof(long long));
     if (eps > 0.0) {

@@ -16,9 +16,10 @@ struct RodLaunch {
     double* FN;                // [N][6] segment force / moment scratch (two-kernel path)
     const int* chunks;         // [n_chunks] base node of every fused-kernel chunk, or NULL
     int n_chunks;
-    // [n_wchunks] base node of every chunk of kWNodes nodes (warp-cooperative force kernel,
-    // systems of at most kWarpForceMaxNodes nodes), or NULL
-    const int* wchunks = nullptr;
+    // [n_wchunks] every chunk of kWNodes nodes of the warp-cooperative force kernel (batches of
+    // at most kWarpForceMaxNodes nodes by default): (base node, nodes of its rod, index of the
+    // base node in the rod, instance), or NULL
+    const int4* wchunks = nullptr;
     int n_wchunks = 0;
     double inv_L;              // 1 / p.L
     // Reference point of the float32 position packs (see rod_kernels.cu): the mean of the
@@ -99,7 +100,7 @@ struct RodWorkspace {
     int2* d_node_info = nullptr;
     int* d_chunks = nullptr;
     int n_chunks = 0;
-    int* d_wchunks = nullptr;
+    int4* d_wchunks = nullptr;
     int n_wchunks = 0;
     double* d_t0 = nullptr;
     long long* d_step = nullptr;

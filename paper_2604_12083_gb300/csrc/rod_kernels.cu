@@ -476,30 +476,54 @@ __global__ void __launch_bounds__(128) rod_forces_warp_kernel(
     double* g64, double* m64, float* Xf, float* gf, float* mf)
 {
     pdl_wait();
+    constexpr int NW = kWNodes + 2;   // the chunk's nodes and one on each side
     __shared__ WSeg sW[kWSegs];
+    __shared__ double sX[NW * 3], sD[NW * 9];   // window node w = node k0 - 1 + w
+    __shared__ double sRX[24];                  // positions of the pack reference nodes
     __shared__ double sref[3];
-    const long long k0 = L.wchunks[blockIdx.x];
+    const int4 ch = L.wchunks[blockIdx.x];   // (k0, M, b0, instance): the same for every thread
+    const long long k0 = ch.x;
+    const int M = ch.y, b0 = ch.z, inst = ch.w;
 #if MRS_DEBUG_BOUNDS
-    if (k0 < 0 || k0 >= L.N) {   // every thread reads the same chunk: the CTA leaves together
-        if (threadIdx.x == 0 && L.err) atomicOr(L.err, MRS_FLAG_BOUNDS);
-        return;
+    {
+        bool bad = k0 < 0 || k0 >= L.N;
+        if (!bad) {
+            const int2 ni0 = L.node_info[k0];
+            bad = !rod_node_ok(ni0, k0, L.N) || ni0.x != b0 || ni0.y != M ||
+                  inst != (int)(k0 / L.nodes_per_inst);
+        }
+        if (bad) {   // every thread sees the same entry: the CTA leaves together
+            if (threadIdx.x == 0 && L.err) atomicOr(L.err, MRS_FLAG_BOUNDS);
+            return;
+        }
     }
 #endif
-    const int2 ni0 = L.node_info[k0];
-    if (!node_checked(L, ni0, k0, L.N)) return;   // the same entry for every thread of the CTA
-    const int M = ni0.y, b0 = ni0.x;              // the rod's nodes, the chunk's first node in it
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int inst = (int)(k0 / L.nodes_per_inst);
     const double ids = (double)(M - 1) * L.inv_L;
     const bool centred = Xf && L.n_ref > 0;
+    // window node w exists when b0 - 1 + w is a node of the rod
+    const int wlo = b0 == 0 ? 1 : 0, whi = min(NW, M - b0 + 1);
+    // one round of loads: the window's positions and frames, the reference nodes' positions
+    for (int idx = threadIdx.x; idx < NW * 12; idx += blockDim.x) {
+        const int wn = idx / 12, r = idx - 12 * (idx / 12);
+        if (wn >= wlo && wn < whi) {
+            const long long k = k0 - 1 + wn;
+            if (r < 3) sX[wn * 3 + r] = X[3 * k + r];
+            else sD[wn * 9 + r - 3] = D[9 * k + r - 3];
+        }
+    }
+    if (warp == 3 && centred && lane < 3 * L.n_ref) {
+        const int i = lane / 3, c = lane - 3 * (lane / 3);
+        sRX[lane] = X[3 * ((size_t)inst * L.nodes_per_inst + L.ref[i]) + c];
+    }
+    __syncthreads();
 
-    // segment s of the chunk is segment b0 - 1 + s of the rod (nodes k0 - 1 + s and k0 + s)
+    // segment s of the chunk is segment b0 - 1 + s of the rod (window nodes s and s + 1)
     const int g = lane / kWSegLanes, sl = lane - kWSegLanes * g;
     const int s = kWSegPerWarp * warp + g;
     const bool seg_valid = warp < 3 && g < kWSegPerWarp && b0 - 1 + s >= 0 && b0 - 1 + s < M - 1;
-    const long long ks = k0 - 1 + s;
-    const double* Xk = X + 3 * (seg_valid ? ks : k0);
-    const double* Dk = D + 9 * (seg_valid ? ks : k0);
+    const double* Xk = sX + 3 * (seg_valid ? s : 0);
+    const double* Dk = sD + 9 * (seg_valid ? s : 0);
 
     if (warp < 3) {
         wseg_frame(Dk, seg_valid, sl, sW[g < kWSegPerWarp ? s : 0]);
@@ -524,19 +548,18 @@ __global__ void __launch_bounds__(128) rod_forces_warp_kernel(
         wseg_forces(L.p, Xk, Dk, ids, seg_valid, sl, sW[g < kWSegPerWarp ? s : 0]);
     } else if (centred && lane < 3) {
         // pack_reference, component `lane`, summed in the same order
-        const double* Xi = X + 3 * (size_t)inst * L.nodes_per_inst;
         double acc = 0.0;
-        for (int i = 0; i < L.n_ref; ++i) acc += Xi[3 * L.ref[i] + lane];
+        for (int i = 0; i < L.n_ref; ++i) acc += sRX[3 * i + lane];
         sref[lane] = acc * L.ref_w;
     }
     __syncthreads();
     if (warp != 3 || lane >= 3 * kWNodes) return;
-    // node phase: node nn of the chunk, component c (node_fn's terms)
+    // node phase: node nn of the chunk (window node nn + 1), component c (node_fn's terms)
     const int nn = lane / 3, c = lane - 3 * (lane / 3);
     const int nb = b0 + nn;
     if (nb >= M) return;
     const long long k = k0 + nn;
-    const double* Xn = X + 3 * (size_t)k;
+    const double* Xn = sX + 3 * (nn + 1);
     const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
     double gv = 0.0, mv = 0.0;
     if (nb < M - 1) {   // segment k+1/2 = chunk segment nn + 1
