@@ -346,7 +346,8 @@ int plan_build(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, doubl
         p->cl = cl;
         P = (long long)p->n_tiles * cl;
     } else {
-        P = ordered_ctas((long long)ctx->num_sms * occ * std::max(1, kc.over), W, max_nu);
+        const long long full = (long long)ctx->num_sms * occ * std::max(1, kc.over);
+        P = balanced_ctas(ordered_ctas(full, W, max_nu), full, W, ctx->num_sms, kc.threads);
     }
     p->P = (int)P;
     const size_t part_floats = kc.cluster ? 1 : (size_t)2 * P * 6 * p->TM;

@@ -122,6 +122,22 @@ inline long long ordered_ctas(long long P, long long W, long long max_nu)
     return P < 1 ? 1 : P;
 }
 
+// CTAs of 256 threads or more (two warps per scheduler each): when the full grid of `full`
+// CTAs would give each fewer than kBalancedUnits of the W units, one CTA per SM (at most P).
+// A second such CTA on an SM shares its schedulers, so with a grid that is not a whole number
+// of CTAs per SM the SMs that hold two set the call's length, and with little work per CTA
+// the finishing CTAs' slot reads weigh more.  Measured on GB300, one system with 256-target
+// tiles (µs per call, capped or full grid -> one CTA per SM): 2560 points 27.5 -> 20.6 (160
+// -> 152 CTAs), 3072 points 31.9 -> 24.9 (192 -> 152), 4096 points 38.9 -> 35.5 (456 -> 152),
+// 6144 points 76.9 -> 72.5; at 8192 points (18 units per CTA) the full grid stays best.
+// Smaller CTAs keep the grid (64-thread CTAs lost 20 % when cut to one per SM).
+constexpr int kBalancedUnits = 12;
+inline long long balanced_ctas(long long P, long long full, long long W, int sms, int threads)
+{
+    if (threads >= 256 && W < (long long)kBalancedUnits * full && P > sms) P = sms;
+    return P;
+}
+
 struct TileDesc {
     int sys;     // system index
     int t0;      // first target (global point index)
