@@ -319,9 +319,11 @@ MRS_API int rod_advance(mrs_ctx* ctx, int64_t N, double* X, double* D, const voi
  * packs hold positions relative to a reference point of the current state (the mean of the
  * middle nodes of up to 8 rods), so the pair sum's accuracy does not depend on where the
  * system sits; results do not depend on how a run is split into calls.
- * scheme MRS_EULER or MRS_RK2 (explicit midpoint on positions and frames).  Instances of at
- * most 128 nodes run all their steps in one fused launch; larger ones replay the steps from CUDA
- * graphs captured once per (rods, scheme) (mrs_ctx_set_fused_steps).  Synchronizes `stream`
+ * scheme MRS_EULER or MRS_RK2 (explicit midpoint on positions and frames).  The steps replay
+ * from CUDA graphs captured once per (rods, scheme).  For systems of up to 4096 nodes they use
+ * the warp-cooperative force kernel, and the small-system pair sum applies the update itself:
+ * two launches per stage (mrs_ctx_set_rod_force_kernel).  The fused one-launch path
+ * (mrs_ctx_set_fused_steps) is taken here only when mode 2 asks for it.  Synchronizes `stream`
  * only at set-up.  Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */
 MRS_API int rod_step(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_params* p,
              double* X, double* D, double t0, double dt, int nsteps, int scheme,
