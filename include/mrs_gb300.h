@@ -322,8 +322,9 @@ MRS_API int rod_advance(mrs_ctx* ctx, int64_t N, double* X, double* D, const voi
  * scheme MRS_EULER or MRS_RK2 (explicit midpoint on positions and frames).  The steps replay
  * from CUDA graphs captured once per (rods, scheme).  For systems of up to 4096 nodes they use
  * the warp-cooperative force kernel, and the small-system pair sum applies the update itself:
- * two launches per stage (mrs_ctx_set_rod_force_kernel).  The fused one-launch path
- * (mrs_ctx_set_fused_steps) is taken here only when mode 2 asks for it.  Synchronizes `stream`
+ * two launches per stage (mrs_ctx_set_rod_force_kernel).  A system takes the fused one-launch
+ * path (mrs_ctx_set_fused_steps) only when the fused-steps mode is 2, or when it has at most
+ * 128 nodes and the force-kernel setting is 1.  Synchronizes `stream`
  * only at set-up.  Errors: MRS_EINVAL, MRS_ENOMEM, MRS_ECUDA. */
 MRS_API int rod_step(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const mrs_rod_params* p,
              double* X, double* D, double t0, double dt, int nsteps, int scheme,
