@@ -109,6 +109,7 @@ constexpr size_t kByteAlign = 256;
 struct RodTable {      // passed by value to the set-up kernel (kernel parameter space)
     int n_rods;
     int off[kMaxRodsPerJob + 1];
+    int coff[kMaxRodsPerJob + 1];   // first chunk of kWNodes nodes of every rod
 };
 
 struct SJob {
@@ -127,17 +128,21 @@ struct SJob {
     double *X = nullptr, *D = nullptr, *Xh = nullptr, *Dh = nullptr;
 };
 
-// Byte-pool layout of a rod job with N nodes.
-size_t rod_bytes(size_t N)
+// Chunks of kWNodes nodes of a rod job (at most one partial chunk per rod).
+size_t rod_chunks_bound(size_t N, int n_rods) { return N / kWNodes + (size_t)n_rods + 1; }
+
+// Byte-pool layout of a rod job with N nodes in n_rods rods.
+size_t rod_bytes(size_t N, int n_rods)
 {
     auto al = [](size_t b) { return (b + kByteAlign - 1) / kByteAlign * kByteAlign; };
-    return al(24 * N) + al(72 * N) + al(24 * N) + al(72 * N) + al(48 * N) + al(8 * N) + 2 * kByteAlign;
+    return al(24 * N) + al(72 * N) + al(24 * N) + al(72 * N) + al(48 * N) + al(8 * N) +
+           al(sizeof(int4) * rod_chunks_bound(N, n_rods)) + 2 * kByteAlign;
 }
 
 }  // namespace
 
-__global__ void serve_rod_setup_kernel(int2* node_info, double* t0, long long* step, int N,
-                                       double t_start, const RodTable tab)
+__global__ void serve_rod_setup_kernel(int2* node_info, int4* wchunks, double* t0, long long* step,
+                                       int N, double t_start, const RodTable tab)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) {
@@ -150,7 +155,10 @@ __global__ void serve_rod_setup_kernel(int2* node_info, double* t0, long long* s
         const int mid = (lo + hi + 1) >> 1;
         if (tab.off[mid] <= k) lo = mid; else hi = mid - 1;
     }
-    node_info[k] = make_int2(k - tab.off[lo], tab.off[lo + 1] - tab.off[lo]);
+    const int idx = k - tab.off[lo], M = tab.off[lo + 1] - tab.off[lo];
+    node_info[k] = make_int2(idx, M);
+    // the warp-cooperative force kernel's chunk table: (base node, rod nodes, index, instance)
+    if (idx % kWNodes == 0) wchunks[tab.coff[lo] + idx / kWNodes] = make_int4(k, M, idx, 0);
 }
 
 }  // namespace mrs
@@ -243,7 +251,7 @@ bool reserve(mrs_server* S, SJob* j)
     size_t po = 0, bo = 0;
     if (!S->pts.alloc(N, &po)) return false;
     if (j->spec.kind == MRS_JOB_ROD) {
-        const size_t nb = rod_bytes(N) / kByteAlign;
+        const size_t nb = rod_bytes(N, j->spec.n_rods) / kByteAlign;
         if (!S->bytes.alloc(nb, &bo)) {
             S->pts.release(po, N);
             return false;
@@ -290,14 +298,18 @@ cudaError_t admit_enqueue(mrs_server* S, SJob* j)
     base += al(48 * N);
     int2* info = (int2*)base;
     base += al(8 * N);
+    int4* wch = (int4*)base;
+    base += al(sizeof(int4) * rod_chunks_bound(N, J.n_rods));
     double* t0 = (double*)base;
     long long* step = (long long*)(base + kByteAlign);
     if ((e = cudaMemcpyAsync(j->X, J.Xr, 24 * N, cudaMemcpyDeviceToDevice, s))) return e;
     if ((e = cudaMemcpyAsync(j->D, J.Dr, 72 * N, cudaMemcpyDeviceToDevice, s))) return e;
     RodTable tab;
     tab.n_rods = J.n_rods;
+    tab.coff[0] = 0;
     for (int r = 0; r <= J.n_rods; ++r) tab.off[r] = (int)j->rod_off[r];
-    serve_rod_setup_kernel<<<(int)((N + 127) / 128), 128, 0, s>>>(info, t0, step, (int)N, J.t0, tab);
+    for (int r = 0; r < J.n_rods; ++r) tab.coff[r + 1] = tab.coff[r] + (tab.off[r + 1] - tab.off[r] + kWNodes - 1) / kWNodes;
+    serve_rod_setup_kernel<<<(int)((N + 127) / 128), 128, 0, s>>>(info, wch, t0, step, (int)N, J.t0, tab);
     if ((e = cudaGetLastError())) return e;
     RodLaunch& L = j->L;
     L.N = (int)N;
@@ -309,8 +321,13 @@ cudaError_t admit_enqueue(mrs_server* S, SJob* j)
     L.p = J.params;
     L.p.lj_sigma = lj_sigma_of(J.params);
     L.FN = FN;
-    L.chunks = nullptr;   // two-kernel force path (no chunk table in the pool)
+    L.chunks = nullptr;   // no thread-per-segment chunk table in the pool: two-kernel force path
     L.n_chunks = 0;
+    // small jobs: the warp-cooperative force and update kernels (the context's setting)
+    const int fk = S->ctx->rod_force_kernel;
+    const bool warp = fk == 2 || (fk == 0 && N <= (size_t)kWarpForceMaxNodes);
+    L.wchunks = warp ? wch : nullptr;
+    L.n_wchunks = tab.coff[J.n_rods];
     L.inv_L = 1.0 / J.params.L;
     set_pack_reference(L, J.n_rods, j->rod_off.data());
     L.segsc = nullptr;    // two-kernel force path: sin(k_w s_mid + f t) per segment
@@ -747,7 +764,7 @@ int serve_submit(mrs_server* S, const mrs_job* job, uint64_t* ticket)
     }
     const size_t N = (size_t)J.n_points;
     if (N > S->pts.capacity() || (long long)((N + S->TM - 1) / S->TM) > S->tile_cap ||
-        (J.kind == MRS_JOB_ROD && rod_bytes(N) / kByteAlign > S->bytes.capacity())) {
+        (J.kind == MRS_JOB_ROD && rod_bytes(N, J.n_rods) / kByteAlign > S->bytes.capacity())) {
         delete j;
         set_error("job of %zu points does not fit the serving pool", N);
         return MRS_EBUSY;
