@@ -101,6 +101,8 @@ class RangeAlloc {
 constexpr int kMaxRodsPerJob = 1024;
 constexpr int kServeConfig = 8;             // 64 threads x 4 targets, packed f32x2 (TM = 256)
 constexpr int kServeSymConfig = 25;         // symmetric, 64 threads x 6 points (TM = 384), 4 waves
+constexpr int kMaxStagesPerIteration = 16;  // rod-only iterations: stages enqueued at once
+constexpr double kIterPairBudget = 1.5e8;   // ... and pair interactions in all (~0.25 ms)
 constexpr double kServeSymShare = 0.03;     // share of the budget for symmetric scratch ...
 constexpr size_t kServeSymMax = (size_t)3 << 30;   // ... up to 3 GiB
 constexpr int kMaxServeTiles = 1 << 20;     // tiles of one iteration's batched launch
@@ -188,6 +190,12 @@ struct mrs_server {
     float* d_colpart = nullptr;
     size_t rowpart_cap = 0, colpart_cap = 0;
     int64_t sym_iterations = 0;
+    // single-system iterations take the library's default configuration for that one system
+    // (as mrs_velocity would): resident CTAs per SM of every ordered configuration, and clusters
+    // of cl CTAs resident at once for the cluster configurations (0: none)
+    int occ_cfg[64] = {};
+    int cl_fit[64][17] = {};
+    size_t partial_cap = 0;   // floats of d_partial
     struct Stage {
         TileDesc* tiles = nullptr;
         SymTile* stiles = nullptr;
@@ -354,16 +362,48 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
             }
         }
     }
-    // rod forces of the current stage, packed into each job's point range
-    for (SJob* j : run) {
-        if (j->spec.kind != MRS_JOB_ROD) continue;
-        const bool half = j->spec.scheme == MRS_RK2 && j->stage == 1;
-        const size_t o = 3 * j->pt_off;
-        e = launch_rod_forces(j->L, half ? j->Xh : j->X, half ? j->Dh : j->D,
-                              half ? 0.5 * j->spec.dt : 0.0, nullptr, nullptr, S->pX + o, S->pf + o,
-                              S->pn + o, s);
-        if (e) return e;
+    // stages this iteration: several when every job it advances is a rod job and none is
+    // waiting for admission, so that small rod jobs do not pay one iteration's host work per
+    // stage; bounded by the jobs' remaining stages (none finishes before the last) and by
+    // kIterPairBudget pair interactions in all (a later arrival waits at most that long)
+    int stages = 1;
+    {
+        bool rods_only = !run.empty();
+        long long rem = kMaxStagesPerIteration;
+        double stage_pairs = 0.0;
+        for (SJob* j : run) {
+            if (j->spec.kind != MRS_JOB_ROD) {
+                rods_only = false;
+                break;
+            }
+            const int per = j->spec.scheme == MRS_RK2 ? 2 : 1;
+            rem = std::min<long long>(rem, (long long)j->spec.nsteps * per - ((long long)j->steps_done * per + j->stage));
+            stage_pairs += (double)j->spec.n_points * (double)j->spec.n_points;
+        }
+        bool queue_empty;
+        {
+            std::lock_guard<std::mutex> g(S->mu);
+            queue_empty = S->waiting.empty();
+        }
+        if (rods_only && queue_empty && stage_pairs > 0.0) {
+            const double fit = std::floor(kIterPairBudget / stage_pairs);
+            stages = (int)std::max<double>(1.0, std::min<double>((double)rem, fit));
+        }
     }
+    // rod forces of the current stage, packed into each job's point range
+    auto enqueue_forces = [&]() -> cudaError_t {
+        for (SJob* j : run) {
+            if (j->spec.kind != MRS_JOB_ROD) continue;
+            const bool half = j->spec.scheme == MRS_RK2 && j->stage == 1;
+            const size_t o = 3 * j->pt_off;
+            e = launch_rod_forces(j->L, half ? j->Xh : j->X, half ? j->Dh : j->D,
+                                  half ? 0.5 * j->spec.dt : 0.0, nullptr, nullptr, S->pX + o, S->pf + o,
+                                  S->pn + o, s);
+            if (e) return e;
+        }
+        return cudaSuccess;
+    };
+    if ((e = enqueue_forces())) return e;
     // work table of the batched pair sum
     mrs_server::Stage& st = S->stage[S->stage_idx];
     S->stage_idx = (S->stage_idx + 1) % 3;
@@ -413,7 +453,41 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
         T.seg0 = (int)nseg;
         nseg += T.nseg;
     }
-    const bool sym = (size_t)sW * kUnitSources * 6 <= S->colpart_cap &&
+    // one system: the configuration a plan for it would choose (cluster kernel, ordered
+    // persistent kernel or symmetric kernel), when the server's buffers hold its tables
+    int ocfg = S->config, oTM = S->TM, ocl = 0;
+    long long oP = -1;
+    if (n_sys == 1) {
+        const long long N = run[0]->spec.n_points;
+        const int64_t off[2] = {0, N};
+        const int c = default_config(S->ctx, 1, off, MRS_F32_COMP);
+        const KernelConfig kc = kConfigs[c];
+        if (!kc.sym && c < 64 && S->occ_cfg[c] > 0) {
+            const int TMc = tile_targets(kc);
+            const long long ntc = (N + TMc - 1) / TMc, nu = (N + kUnitSources - 1) / kUnitSources;
+            if (kc.cluster) {
+                int cl = (int)std::min<long long>(kc.cluster, nu);
+                while (cl > 1 && S->cl_fit[c][cl] < ntc) --cl;
+                if (ntc <= S->tile_cap && S->cl_fit[c][cl] > 0) {
+                    ocfg = c;
+                    oTM = TMc;
+                    ocl = cl;
+                    oP = ntc * cl;
+                }
+            } else {
+                const long long full = (long long)S->ctx->num_sms * S->occ_cfg[c] * std::max(1, kc.over);
+                const long long Wc = ntc * nu;
+                const long long P = balanced_ctas(ordered_ctas(full, Wc, nu), full, Wc, S->ctx->num_sms,
+                                                  kc.threads);
+                if (ntc <= S->tile_cap && (size_t)2 * P * 6 * TMc <= S->partial_cap) {
+                    ocfg = c;
+                    oTM = TMc;
+                    oP = P;
+                }
+            }
+        }
+    }
+    const bool sym = oP < 0 && (size_t)sW * kUnitSources * 6 <= S->colpart_cap &&
                      (size_t)nseg * S->sTM * 6 <= S->rowpart_cap;
     int nt = 0;
     long long W = 0, max_nu = 0;
@@ -422,11 +496,11 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
             SJob* j = run[q];
             const long long N = j->spec.n_points;
             const int nu = (int)((N + kUnitSources - 1) / kUnitSources);
-            for (long long t = 0; t < N; t += S->TM) {
+            for (long long t = 0; t < N; t += oTM) {
                 TileDesc& T = st.tiles[nt++];
                 T.sys = q;
                 T.t0 = (int)(j->pt_off + t);
-                T.tn = (int)std::min<long long>(S->TM, N - t);
+                T.tn = (int)std::min<long long>(oTM, N - t);
                 T.s0 = (int)j->pt_off;
                 T.sn = (int)N;
                 T.nu = nu;
@@ -441,76 +515,92 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
     }
     if ((e = cudaMemcpyAsync(S->d_sc, st.sc, n_sys * sizeof(SysConst), cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaEventRecord(st.used, s))) return e;
-    if (sym) {
-        SymLaunch L;
-        L.tiles = S->d_stiles;
-        L.n_tiles = snt;
-        L.TM = S->sTM;
-        L.W = sW;
-        L.P = sP;
-        L.U0 = 0;                 // one pass over every tile of the iteration
-        L.ta = 0;
-        L.tb = snt;
-        L.tc = snt;
-        L.acc = nullptr;
-        L.n_points = (long long)S->pts.capacity();
-        L.col_units = (long long)(S->colpart_cap / (kUnitSources * 6));
-        L.row_segs = (long long)(S->rowpart_cap / ((size_t)S->sTM * 6));
-        L.sc = S->d_sc;
-        L.X = S->pX;
-        L.f = S->pf;
-        L.n = S->pn;
-        L.u = S->pu;
-        L.w = S->pw;
-        L.rowpart = S->d_rowpart;
-        L.colpart = S->d_colpart;
-        L.err = S->ctx->d_err;
-        if ((e = launch_mrs_sym(S->sym_config, true, L, s))) return e;
-    } else {
-        MrsLaunch L;
-        L.tiles = S->d_tiles;
-        L.n_tiles = nt;
-        L.W = W;
-        L.P = (int)ordered_ctas(S->P, W, max_nu);
-        L.sc = S->d_sc;
-        L.X = S->pX;
-        L.f = S->pf;
-        L.n = S->pn;
-        L.Xt = S->pX;
-        L.u = S->pu;
-        L.w = S->pw;
-        L.partial = S->d_partial;
-        L.counters = S->d_counters;
-        L.err = S->ctx->d_err;
-        L.n_points = (long long)S->pts.capacity();
-        if ((e = launch_mrs_f32(S->config, true, L, s))) return e;
-    }
-    // stage updates and copy-out
-    for (SJob* j : run) {
-        const size_t N = (size_t)j->spec.n_points, o = 3 * j->pt_off;
-        bool done = false;
-        if (j->spec.kind == MRS_JOB_VELOCITY) {
-            if ((e = cudaMemcpyAsync(j->spec.u, S->pu + o, 12 * N, cudaMemcpyDeviceToDevice, s))) return e;
-            if ((e = cudaMemcpyAsync(j->spec.w, S->pw + o, 12 * N, cudaMemcpyDeviceToDevice, s))) return e;
-            done = true;
+    // the batched pair sum of the iteration's tables
+    auto enqueue_pair = [&]() -> cudaError_t {
+        if (sym) {
+            SymLaunch L;
+            L.tiles = S->d_stiles;
+            L.n_tiles = snt;
+            L.TM = S->sTM;
+            L.W = sW;
+            L.P = sP;
+            L.U0 = 0;                 // one pass over every tile of the iteration
+            L.ta = 0;
+            L.tb = snt;
+            L.tc = snt;
+            L.acc = nullptr;
+            L.n_points = (long long)S->pts.capacity();
+            L.col_units = (long long)(S->colpart_cap / (kUnitSources * 6));
+            L.row_segs = (long long)(S->rowpart_cap / ((size_t)S->sTM * 6));
+            L.sc = S->d_sc;
+            L.X = S->pX;
+            L.f = S->pf;
+            L.n = S->pn;
+            L.u = S->pu;
+            L.w = S->pw;
+            L.rowpart = S->d_rowpart;
+            L.colpart = S->d_colpart;
+            L.err = S->ctx->d_err;
+            if ((e = launch_mrs_sym(S->sym_config, true, L, s))) return e;
         } else {
-            const double dt = j->spec.dt;
-            if (j->spec.scheme == MRS_RK2 && j->stage == 0) {
-                e = launch_rod_update(j->L, j->X, j->D, S->pu + o, S->pw + o, 0.5 * dt, j->Xh, j->Dh, false, s);
-                j->stage = 1;
-            } else {
-                e = launch_rod_update(j->L, j->X, j->D, S->pu + o, S->pw + o, dt, j->X, j->D, true, s);
-                j->stage = 0;
-                j->steps_done += 1;
+            MrsLaunch L;
+            L.tiles = S->d_tiles;
+            L.n_tiles = nt;
+            L.W = W;
+            L.P = (int)ordered_ctas(S->P, W, max_nu);
+            L.sc = S->d_sc;
+            L.X = S->pX;
+            L.f = S->pf;
+            L.n = S->pn;
+            L.Xt = S->pX;
+            L.u = S->pu;
+            L.w = S->pw;
+            L.partial = S->d_partial;
+            L.counters = S->d_counters;
+            L.err = S->ctx->d_err;
+            L.n_points = (long long)S->pts.capacity();
+            if (oP >= 0) {   // the one system's own configuration
+                L.P = (int)oP;
+                L.cl = ocl;
             }
-            if (e) return e;
-            if (j->steps_done == j->spec.nsteps) {
-                if ((e = cudaMemcpyAsync(j->spec.Xr, j->X, 24 * N, cudaMemcpyDeviceToDevice, s))) return e;
-                if ((e = cudaMemcpyAsync(j->spec.Dr, j->D, 72 * N, cudaMemcpyDeviceToDevice, s))) return e;
-                done = true;
-            }
+            if ((e = launch_mrs_f32(ocfg, true, L, s))) return e;
         }
-        if (done) finishing.push_back(j);
+        return cudaSuccess;
+    };
+    // stage updates and copy-out
+    auto enqueue_updates = [&]() -> cudaError_t {
+        for (SJob* j : run) {
+            const size_t N = (size_t)j->spec.n_points, o = 3 * j->pt_off;
+            bool done = false;
+            if (j->spec.kind == MRS_JOB_VELOCITY) {
+                if ((e = cudaMemcpyAsync(j->spec.u, S->pu + o, 12 * N, cudaMemcpyDeviceToDevice, s))) return e;
+                if ((e = cudaMemcpyAsync(j->spec.w, S->pw + o, 12 * N, cudaMemcpyDeviceToDevice, s))) return e;
+                done = true;
+            } else {
+                const double dt = j->spec.dt;
+                if (j->spec.scheme == MRS_RK2 && j->stage == 0) {
+                    e = launch_rod_update(j->L, j->X, j->D, S->pu + o, S->pw + o, 0.5 * dt, j->Xh, j->Dh, false, s);
+                    j->stage = 1;
+                } else {
+                    e = launch_rod_update(j->L, j->X, j->D, S->pu + o, S->pw + o, dt, j->X, j->D, true, s);
+                    j->stage = 0;
+                    j->steps_done += 1;
+                }
+                if (e) return e;
+                if (j->steps_done == j->spec.nsteps) {
+                    if ((e = cudaMemcpyAsync(j->spec.Xr, j->X, 24 * N, cudaMemcpyDeviceToDevice, s))) return e;
+                    if ((e = cudaMemcpyAsync(j->spec.Dr, j->D, 72 * N, cudaMemcpyDeviceToDevice, s))) return e;
+                    done = true;
+                }
+            }
+            if (done) finishing.push_back(j);
+        }
+        return cudaSuccess;
+    };
+    for (int k = 0; k < stages; ++k) {
+        if (k > 0 && (e = enqueue_forces())) return e;
+        if ((e = enqueue_pair())) return e;
+        if ((e = enqueue_updates())) return e;
     }
     if (!finishing.empty()) {
         std::vector<SJob*> keep;
@@ -522,7 +612,7 @@ cudaError_t run_iteration(mrs_server* S, std::vector<SJob*>& finishing)
     std::lock_guard<std::mutex> g(S->mu);
     S->iterations += 1;
     S->sym_iterations += sym ? 1 : 0;
-    S->pairs += pairs;
+    S->pairs += pairs * stages;
     return cudaSuccess;
 }
 
@@ -686,6 +776,24 @@ int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int ma
         return MRS_ECUDA;
     }
     S->sP = ctx->num_sms * occ * std::max(1, kConfigs[S->sym_config].over);
+    for (int c = 0; c < kNumConfigs && c < 64; ++c) {
+        if (kConfigs[c].sym) continue;
+        int oc = 0;
+        if (occupancy_f32(c, true, &oc) != MRS_OK) {
+            cudaGetLastError();
+            oc = 0;
+        }
+        S->occ_cfg[c] = oc;
+        if (kConfigs[c].cluster && oc > 0)
+            for (int cl = 1; cl <= 16 && cl <= kConfigs[c].cluster; ++cl) {
+                int mc = 0;
+                if (cluster_setup_f32(c, true, cl, &mc) != MRS_OK) {
+                    cudaGetLastError();   // a refused cluster shape: that size is not used
+                    mc = 0;
+                }
+                S->cl_fit[c][cl] = mc;
+            }
+    }
     S->colpart_cap = sym_bytes / 3 * 2 / sizeof(float);
     S->rowpart_cap = sym_bytes / 3 / sizeof(float);
     // tiles of the symmetric table (TM = sTM >= TM) never outnumber the ordered ones
@@ -695,7 +803,7 @@ int serve_create(mrs_server** srv, mrs_ctx* ctx, size_t hbm_budget_bytes, int ma
         (st = dalloc(&S->pn, 3 * pt_cap)) || (st = dalloc(&S->pu, 3 * pt_cap)) ||
         (st = dalloc(&S->pw, 3 * pt_cap)) || (st = dalloc(&S->d_bytes, by_cap * kByteAlign)) ||
         (st = dalloc(&S->d_tiles, (size_t)S->tile_cap)) || (st = dalloc(&S->d_sc, (size_t)S->sys_cap)) ||
-        (st = dalloc(&S->d_partial, (size_t)2 * S->P * 6 * S->TM)) ||
+        (st = dalloc(&S->d_partial, S->partial_cap = (size_t)2 * S->P * 6 * S->TM)) ||
         (st = dalloc(&S->d_counters, (size_t)S->tile_cap)) ||
         (st = dalloc(&S->d_stiles, (size_t)S->tile_cap)) ||
         (st = dalloc(&S->d_rowpart, S->rowpart_cap)) || (st = dalloc(&S->d_colpart, S->colpart_cap))) {
