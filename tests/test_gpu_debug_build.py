@@ -1,7 +1,8 @@
 """The debug build (index checks compiled in, MRS_GB300_DEBUG=1) on the GPU, in a process of its
 own: on valid inputs no check fires (mrs_device_status stays clear of MRS_FLAG_BOUNDS) and the
 results match the FP64 oracle as the release build's do -- a ragged batch through every kernel
-configuration, a symmetric plan in many passes, fused and graph rod stepping, and a served mix."""
+configuration, a symmetric plan in many passes, fused and graph rod stepping (both force
+kernels), and a served mix."""
 import json
 import os
 import subprocess
@@ -46,20 +47,23 @@ for pass_bytes in (192 << 20, 3 * 768):
             a, b = p.offsets[s], p.offsets[s + 1]
             worst = max(worst, rel(uu[a:b], ur[a:b]), rel(ww[a:b], wr[a:b]))
 ctx.set_sym_pass_bytes(192 << 20)
-# rod stepping: fused and graph paths against the oracle
+# rod stepping: the fused path, the graph path with the warp-cooperative kernels (and the pair
+# sum applying the update) and with one thread per segment, against the oracle
 rs = W.rod_system(95, 3, 40, box=2.0)
 cfg = dict(W.ROD_PLAIN, a=(2e-3,) * 3, b=(20.0,) * 3)
 gp = mrs.RodParams.make(cfg["L"], cfg["a"], cfg["b"], cfg["wave_A"], cfg["wave_k"], cfg["wave_f"], 1.0, rs.eps)
 op = oracle.RodParams.make(cfg["L"], cfg["a"], cfg["b"], cfg["wave_A"], cfg["wave_k"], cfg["wave_f"])
 Xo, _ = oracle.rod_step(rs.rod_off, rs.X, rs.D, op, rs.eps, 1.0, 0.0, 2e-6, 20, oracle.RK2)
 rod_worst = 0.0
-for mode in (2, 0):
+for mode, fk in ((2, 0), (0, 0), (0, 1)):
     ctx.set_fused_steps(mode)
+    ctx.set_rod_force_kernel(fk)
     Xd, Dd = torch.from_numpy(rs.X.copy()).cuda(), torch.from_numpy(rs.D.copy()).cuda()
     mrs.rod_step(ctx, rs.rod_off, gp, Xd, Dd, 0.0, 2e-6, 20, mrs.MRS_RK2)
     torch.cuda.synchronize()
     rod_worst = max(rod_worst, rel(Xd.cpu().numpy() - rs.X, Xo - rs.X))
 ctx.set_fused_steps(1)
+ctx.set_rod_force_kernel(0)
 # a small served mix
 srv = mrs.Server(ctx, 1 << 30, 16)
 q = W.single_system(seed=96, n_fil=4, M=256, box=4.0)
