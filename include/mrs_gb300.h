@@ -234,9 +234,15 @@ MRS_API int mrs_velocity_noalloc(int64_t n_points, const float* X, const float* 
  *           N^2 / (2 TM) * 24 bytes for one system of N points, TM = threads x points per
  *           thread of the configuration: 384 for the default symmetric one, up to 1536); beyond
  *           the context's pass size (mrs_ctx_set_sym_pass_bytes) the plan runs in passes.
+ *           Configurations 27 and 28 are the small-system cluster kernel (ordered): one
+ *           thread-block cluster of up to 16 CTAs per tile of 32 (27) or 64 (28) targets, each
+ *           CTA over a share of the tile's sources split among 8 (4) thread groups, the CTAs'
+ *           partials summed through distributed shared memory in rank order (deterministic, no
+ *           scratch).  The cluster size is the largest for which all tiles' clusters are
+ *           resident at once.  The library's choice for a few systems of up to 2560 points.
  * A plan owns device tables and scratch; mrs_plan_execute allocates nothing and launches one
- * persistent kernel (plus the reduction kernel for a symmetric configuration; for MRS_F64 one
- * plain kernel).  Executions of the same plan must not overlap on the GPU.  Arguments as for
+ * kernel (the persistent or cluster pair kernel, plus the reduction kernel for a symmetric
+ * configuration; for MRS_F64 one plain kernel).  Executions of the same plan must not overlap on the GPU.  Arguments as for
  * mrs_velocity. */
 MRS_API int mrs_plan_create(mrs_ctx* ctx, int n_sys, const int64_t* offsets, double mu, double eps,
                     const double* eps_per_sys, int precision, int config, mrs_plan** plan);
