@@ -246,6 +246,9 @@ def test_rod_invalid_arguments(ctx):
         mrs.rod_step(ctx, [0, 1, 4], gp, X, D, 0.0, 1e-6, 1, 0)      # 1-node rod
     with pytest.raises(mrs.MrsError):
         ctx.set_fused_steps(3)                                        # modes are 0, 1, 2
+    for bad in (-1, 3):
+        with pytest.raises(mrs.MrsError):
+            ctx.set_rod_force_kernel(bad)                             # modes are 0, 1, 2
     cfg = dict(W.ROD_PLAIN)
     zero_L = mrs.RodParams.make(0.0, cfg["a"], cfg["b"], cfg["wave_A"], cfg["wave_k"], cfg["wave_f"], 1.0, 0.01)
     nan_a = mrs.RodParams.make(1.0, (float("nan"),) * 3, cfg["b"], cfg["wave_A"], cfg["wave_k"],
