@@ -70,8 +70,10 @@ int default_ordered_config(int n_sys, const int64_t* offsets)
     return 9;
 }
 
-// Symmetric configuration used by default.
+// Symmetric configurations used by default: 64 threads x 6 points launched as 4 waves of CTAs,
+// and the same as one wave for systems with fewer work units.
 constexpr int kDefaultSymConfig = 25;
+constexpr int kOneWaveSymConfig = 23;
 
 // Work units and column-partial bytes of a symmetric plan with tiles of TM points.
 static double sym_units(int n_sys, const int64_t* offsets, int TM)
@@ -102,6 +104,11 @@ int default_config(mrs_ctx* ctx, int n_sys, const int64_t* offsets, int precisio
     const double units = sym_units(n_sys, offsets, kc.threads * kc.tpt);
     const double ctas = 3.0 * (ctx ? ctx->num_sms : 152);
     if (all > 0 && big >= 0.5 * all && units >= 32.0 * ctas) return kDefaultSymConfig;
+    // fewer units: the same tiles launched as one wave of CTAs still beat the ordered kernel
+    // from ~12 units per resident CTA (one system, µs per call, this / default ordered:
+    // 12288 points 248.6 / 260.8, 16384 points 422.3 / 444.2; at 8192 points, ~6 units per
+    // CTA, 117.0 / 118.2 -- kept ordered)
+    if (all > 0 && big >= 0.5 * all && units >= 12.0 * ctas) return kOneWaveSymConfig;
     return default_ordered_config(n_sys, offsets);
 }
 

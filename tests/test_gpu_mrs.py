@@ -407,6 +407,20 @@ def test_cluster_separate_targets(ctx, orc, config):
     assert per_target_max(u, ur) < PER_TARGET and per_target_max(w, wr) < PER_TARGET
 
 
+def test_default_configuration_by_size(ctx):
+    """The library's choice for one system, as measured on GB300: the cluster kernel up to
+    2560 points (32-target tiles up to 1536), the ordered 256 x 1 kernel up to 8192, the
+    symmetric kernel as one wave of CTAs from ~12 work units per resident CTA (12288, 16384)
+    and as four waves beyond (32768, the bench system)."""
+    from paper_2604_12083_gb300 import mrs
+    for N, expect in ((1000, 27), (2048, 28), (4096, 14), (8192, 14), (12288, 23), (16384, 23),
+                      (32768, 25)):
+        pl = mrs.Plan(ctx, np.array([0, N], np.int64), 1.0, 0.01, precision=mrs.MRS_F32_COMP)
+        got = pl.info()["config"]
+        pl.close()
+        assert got == expect, (N, got, expect)
+
+
 def test_nonfinite_inputs_raise_the_device_flag(ctx):
     """A NaN force makes non-finite velocities; the context's device flag reports it once."""
     from paper_2604_12083_gb300 import mrs, workloads as W
