@@ -386,10 +386,9 @@ MRS_API int parareal_run(mrs_ctx* ctx, int n_rods, const int64_t* rod_off, const
  * produced their input states (the sweep streams its results downstream), overlapping the
  * serial coarse/correction sweep with fine work.  The next iteration's fine solves are queued
  * before the current increment is known; if the current iteration converges, that work is
- * discarded.  When the fine solves of all slices fill the GPU (n_points x n_slices >= 65536)
- * and either (second iteration) the first increment is below 1000 tol or (from the third
- * iteration on) the last two increments extrapolate geometrically below tol, the current
- * increment is read first and the next fine solves are queued only if needed.  All ordering
+ * discarded.  When either (second iteration) the first increment is below 1000 tol or (from
+ * the third iteration on) the last two increments extrapolate geometrically below tol, the
+ * current increment is read first and the next fine solves are queued only if needed.  All ordering
  * is by CUDA events between streams (no device-side waiting).
  * Arguments, outputs and errors as for parareal_run; group_size in 1..n_slices. */
 MRS_API int parareal_run_pipelined(mrs_ctx* ctx, int n_rods, const int64_t* rod_off,
