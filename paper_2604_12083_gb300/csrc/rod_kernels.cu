@@ -595,26 +595,12 @@ __global__ void __launch_bounds__(128) rod_forces_warp_kernel(
 __device__ __forceinline__ void rodrigues(const double* D0, double wx, double wy, double wz,
                                           double h, double* D1)
 {
-    const double w2 = wx * wx + wy * wy + wz * wz;
-    if (w2 == 0.0) {
+    double ct, a, b;   // rodrigues_coefficients (rod_update.cuh)
+    if (!rodrigues_coefficients(wx, wy, wz, h, ct, a, b)) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) D1[q] = D0[q];
         return;
     }
-    const double q = w2 * h * h;   // theta^2
-    double ct, sc, cc;             // cos(theta), sin(theta)/theta, (1 - cos(theta))/theta^2
-    if (q < 1e-3) {
-        sc = 1.0 + q * (-1.0 / 6.0 + q * (1.0 / 120.0 + q * (-1.0 / 5040.0 + q * (1.0 / 362880.0))));
-        cc = 0.5 + q * (-1.0 / 24.0 + q * (1.0 / 720.0 + q * (-1.0 / 40320.0 + q * (1.0 / 3628800.0))));
-        ct = 1.0 - q * cc;
-    } else {
-        const double th = sqrt(q);
-        double st;
-        sincos(th, &st, &ct);
-        sc = st / th;
-        cc = (1.0 - ct) / q;
-    }
-    const double a = sc * h, b = cc * h * h;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const double* v = D0 + 3 * i;

@@ -11,15 +11,15 @@
 
 namespace mrs {
 
-// Component c of the new director i, from the old director i = (v0, v1, v2).
-__device__ __forceinline__ double rodrigues_entry(double v0, double v1, double v2, double wx, double wy,
-                                                  double wz, double h, int c)
+// The formula's three coefficients for w and h: d_i' = ct d_i + a (w x d_i) + b (w.d_i) w.
+// Returns false (and leaves them unset) when w = 0.
+__device__ __forceinline__ bool rodrigues_coefficients(double wx, double wy, double wz, double h,
+                                                       double& ct, double& a, double& b)
 {
-    const double vc = c == 0 ? v0 : c == 1 ? v1 : v2;
     const double w2 = wx * wx + wy * wy + wz * wz;
-    if (w2 == 0.0) return vc;
+    if (w2 == 0.0) return false;
     const double q = w2 * h * h;   // theta^2
-    double ct, sc, cc;             // cos(theta), sin(theta)/theta, (1 - cos(theta))/theta^2
+    double sc, cc;                 // sin(theta)/theta, (1 - cos(theta))/theta^2
     if (q < 1e-3) {
         sc = 1.0 + q * (-1.0 / 6.0 + q * (1.0 / 120.0 + q * (-1.0 / 5040.0 + q * (1.0 / 362880.0))));
         cc = 0.5 + q * (-1.0 / 24.0 + q * (1.0 / 720.0 + q * (-1.0 / 40320.0 + q * (1.0 / 3628800.0))));
@@ -31,7 +31,18 @@ __device__ __forceinline__ double rodrigues_entry(double v0, double v1, double v
         sc = st / th;
         cc = (1.0 - ct) / q;
     }
-    const double a = sc * h, b = cc * h * h;
+    a = sc * h;
+    b = cc * h * h;
+    return true;
+}
+
+// Component c of the new director i, from the old director i = (v0, v1, v2).
+__device__ __forceinline__ double rodrigues_entry(double v0, double v1, double v2, double wx, double wy,
+                                                  double wz, double h, int c)
+{
+    const double vc = c == 0 ? v0 : c == 1 ? v1 : v2;
+    double ct, a, b;
+    if (!rodrigues_coefficients(wx, wy, wz, h, ct, a, b)) return vc;
     const double wv = b * (wx * v0 + wy * v1 + wz * v2);
     // component c of w x d_i = wA vB - wB vA: (wy v2 - wz v1, wz v0 - wx v2, wx v1 - wy v0)
     const double wA = c == 0 ? wy : c == 1 ? wz : wx, vB = c == 0 ? v2 : c == 1 ? v0 : v1;
