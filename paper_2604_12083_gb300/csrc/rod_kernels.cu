@@ -352,6 +352,8 @@ struct WSeg {          // per-segment shared scratch of rod_forces_warp_kernel
     double A[9];       // D_{k+1} D_k^T
     double S[9];       // its principal square root
     double Dh[9];      // mid frame S D_k
+    double q[4];       // quaternion of A (before the sign is fixed)
+    double h[4];       // half-angle quaternion (a, b, c, d)
     double c[6];       // F_i (0..2), N_i (3..5)
     double FN[6];      // F (lab), N (lab)
     double om2;        // Omega_2 at the segment midpoint
@@ -368,10 +370,10 @@ __device__ __forceinline__ double sel4(int i, double a, double b, double c, doub
     return i == 0 ? a : i == 1 ? b : i == 2 ? c : d;
 }
 
-// Segment warps, first part: A (nine lanes), its quaternion and the half-angle quaternion (every
-// lane of the group: rot_to_quat and rot_sqrt_dev without branches, so that the three groups of
-// a warp, which may take different branches, run one instruction stream), S (nine lanes) and
-// Dh = S D_k (nine lanes).
+// Segment warps, first part: A (nine lanes); the quaternion of A and the half-angle quaternion
+// (rot_to_quat and rot_sqrt_dev without branches, so that the three groups of a warp, which may
+// take different branches, run one instruction stream: every lane forms the branch, x and the
+// norm, lane j < 4 component j); S (nine lanes) and Dh = S D_k (nine lanes).
 __device__ __forceinline__ void wseg_frame(const double* __restrict__ Dk, bool valid, int sl, WSeg& W)
 {
     const double* Dk1 = Dk + 9;
@@ -395,11 +397,10 @@ __device__ __forceinline__ void wseg_frame(const double* __restrict__ Dk, bool v
         const double u3 = br == 0 ? 0.0 : flip_if(A[8], br != 3);
         const double x = fmax(((1.0 + u1) + u2) + u3, 0.0), ir = rsqrt(x);
         const double s = 0.5 * ir;
-        double q[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            // component j: x s on the branch's own component, else (A[p] +- A[m]) s, the pair
-            // depending on {br, j} only
+        if (sl < 4) {
+            // component j = sl: x s on the branch's own component, else (A[p] +- A[m]) s, the
+            // pair depending on {br, j} only
+            const int j = sl;
             const int key = br < j ? 4 * br + j : 4 * j + br;
             const double P = j == br ? x
                              : key == 1 ? A[7] : key == 2 ? A[2] : key == 3 ? A[3]
@@ -407,17 +408,26 @@ __device__ __forceinline__ void wseg_frame(const double* __restrict__ Dk, bool v
             const double M = j == br ? 0.0
                              : key == 1 ? -A[5] : key == 2 ? -A[6] : key == 3 ? -A[1]
                              : key == 6 ? A[3] : key == 7 ? A[6] : A[7];
-            q[j] = (P + M) * s;
+            W.q[j] = (P + M) * s;
         }
-        const bool ng = q[0] < 0.0;   // w >= 0
-        const double q0 = flip_if(q[0], ng), q1 = flip_if(q[1], ng), q2 = flip_if(q[2], ng),
-                     q3 = flip_if(q[3], ng);
+    }
+    __syncwarp();
+    if (valid) {
+        // half-angle quaternion (1 + q) / |1 + q| with w >= 0: every lane the norm, lane j < 4
+        // component j
+        const bool ng = W.q[0] < 0.0;
+        const double q0 = flip_if(W.q[0], ng), q1 = flip_if(W.q[1], ng), q2 = flip_if(W.q[2], ng),
+                     q3 = flip_if(W.q[3], ng);
         const double w1 = 1.0 + q0;
         const double inv = rsqrt(w1 * w1 + q1 * q1 + q2 * q2 + q3 * q3);
-        a = w1 * inv;
-        b = q1 * inv;
-        c = q2 * inv;
-        d = q3 * inv;
+        if (sl < 4) W.h[sl] = (sl == 0 ? w1 : sl == 1 ? q1 : sl == 2 ? q2 : q3) * inv;
+    }
+    __syncwarp();
+    if (valid) {
+        a = W.h[0];
+        b = W.h[1];
+        c = W.h[2];
+        d = W.h[3];
     }
     if (valid && sl < 9) {
         // S[e] = alpha + beta (x1 y1 +- x2 y2) with (x1, y1, x2, y2) from (a, b, c, d):
