@@ -111,8 +111,10 @@ MRS_API int mrs_ctx_set_fused_steps(mrs_ctx* ctx, int enable);
  * node phase), which shortens the path per scheduler and uses more schedulers; the
  * thread-per-segment kernel does the least float64 work in all.  mode = 0 (the default):
  * warp-cooperative for batches of at most 4096 nodes, thread per segment above; 1: always one
- * thread per segment; 2: always warp-cooperative.  Both compute the same expressions; results
- * agree to float64 rounding.  Takes effect for calls made afterwards (captured step graphs are
+ * thread per segment; 2: always warp-cooperative.  With the warp-cooperative kernels the frame
+ * update is warp-cooperative too (nine lanes per node), and in rod stepping the small-system
+ * pair sum applies it to the nodes it completes; with 1 it runs as its own thread-per-node
+ * kernel.  Both compute the same expressions; results agree to float64 rounding.  Takes effect for calls made afterwards (captured step graphs are
  * kept per setting).  Host only.  Errors: MRS_EINVAL (mode outside 0..2). */
 MRS_API int mrs_ctx_set_rod_force_kernel(mrs_ctx* ctx, int mode);
 
