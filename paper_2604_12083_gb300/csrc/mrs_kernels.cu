@@ -448,17 +448,20 @@ mrs_f32_persistent(const MrsLaunch L)
 
 // ---------------------------------------------------------------------------------------------
 // Cluster kernel for small systems (KernelConfig::cluster > 0).  One thread-block cluster of
-// L.cl CTAs per target tile of BLOCK targets (one per thread); CTA r of the cluster sweeps the
-// units [nu r / cl, nu (r+1) / cl) of the tile's sources with the packed inner loop and the
-// per-chunk Kahan folding of mrs_f32_persistent, and leaves its partial (sum - compensation,
-// one float per target and component) in its own shared memory.  After a cluster barrier, CTA r
-// reduces targets [r tpr, (r+1) tpr) of the tile, tpr = ceil(BLOCK / cl): it reads the partial
-// of every CTA of the cluster through distributed shared memory (mapa + ld.shared::cluster) and
-// sums them in rank order with float32 Kahan, as the persistent kernel's finishing CTA sums its
-// slots.  A second barrier keeps every CTA resident until its partials have been read.  For a
-// system of a few hundred to a few thousand points this replaces the scratch slots in global
-// memory, the atomic tile counter and the finishing CTA's reads with on-chip traffic: the call
-// is then a load of the sources, the sweep and two cluster barriers.
+// L.cl CTAs per target tile of TM targets; a CTA has TM x G threads, G groups of TM threads with
+// one target each.  CTA r of the cluster sweeps the units [nu r / cl, nu (r+1) / cl) of the
+// tile's sources, group g taking every G-th 4-source block of each staged chunk, with the
+// packed inner loop and the per-chunk Kahan folding of mrs_f32_persistent.  The groups'
+// partials (sum - compensation) are summed in group order in shared memory into the CTA's
+// partial, one float per target and component.  After a cluster barrier, CTA r reduces targets
+// [r tpr, (r+1) tpr) of the tile, tpr = ceil(TM / cl): it reads the partial of every CTA of the
+// cluster through distributed shared memory (mapa + ld.shared::cluster) and sums them in rank
+// order with float32 Kahan, as the persistent kernel's finishing CTA sums its slots.  A second
+// barrier keeps every CTA resident until its partials have been read.  For a system of a few
+// hundred to a few thousand points this replaces the scratch slots in global memory, the
+// atomic tile counter and the finishing CTA's reads with on-chip traffic: the call is then a
+// load of the sources, the sweep and two cluster barriers, with G warps per tile and SM for
+// latency hiding.
 //
 // Every thread of every CTA reaches both barriers: nothing returns early (a CTA with no units
 // contributes zero partials; the debug build's index checks skip work instead of returning).
